@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Throughput of the ORCA step on GB300: agent-steps/s.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--workload clusters_1m|shared_space_65k|open_square_1k]
+
+A step is one synchronous ORCA update of every agent of the workload (grid
+binning, k-nearest neighbours, ORCA half-planes, velocity LP with the
+least-penetration fallback, integration), through the C ABI, from
+device-resident state.  Default workload: 1,000,000 agents in 64 Gaussian
+clusters over 2 x 2 km (10,000 vehicles).  L2 (129 MB) is flushed before
+every timed step by writing a 256 MB buffer outside the timed events.
+
+Under torchrun every rank runs an independent replica (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+
+--impl reference times the FP64 CPU oracle on this host's cores on a
+bounded sample of agents per step (the reference arm of this benchmark).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "agent-steps/s"
+
+# Algorithmic FP32 operations per counted item (add/sub/mul/div/sqrt = 1,
+# fused multiply-add = 2), read off the device code of the solve kernel:
+#   candidate key test: 2 sub, 2 mul, 1 add                         =  5
+#   ORCA half-plane: relative state 5, obstacle test 13, cut-off or
+#     leg construction 16-30, leg side filter 9, placement 4       = 50
+#   LP pair evaluation: 2 determinants, 1 divide, 1 bound           = 10
+#   per agent: preferred velocity 10, disc clip 6, integration 4,
+#     1D set-ups amortised 10                                       = 30
+FLOPS_CAND, FLOPS_LINE, FLOPS_PAIR, FLOPS_AGENT = 5, 50, 10, 30
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def _scene(name):
+    from paper_2008_11578_gb300 import scenes
+    if name == "clusters_1m":
+        return scenes.clusters(), dict(workload="clusters_1m", agents=1_000_000,
+                                       vehicles=10_000, area_m="2000x2000",
+                                       clusters=64, sigma_m=20.0)
+    if name == "shared_space_65k":
+        return scenes.shared_space(), dict(workload="shared_space_65k", agents=65_000,
+                                           vehicles=1_000, area_m="500x500")
+    if name == "open_square_1k":
+        return scenes.open_square(), dict(workload="open_square_1k", agents=1_000,
+                                          vehicles=0, area_m="50x50")
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu_index), "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on this host's cores, bounded sample per step."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    scene, cfg = _scene(args.workload)
+    oracle.build()
+    cores = oracle.num_threads()
+    rng = np.random.default_rng(0)
+    # size the per-step sample so one step takes about 2 s of CPU time
+    probe = np.sort(rng.choice(scene.n, min(scene.n, 256), replace=False))
+    t0 = time.perf_counter()
+    oracle.step(scene, sel=probe)
+    per_agent = (time.perf_counter() - t0) / len(probe)
+    m = int(min(scene.n, max(64, 2.0 / max(per_agent, 1e-9))))
+    for _ in range(args.warmup):
+        oracle.step(scene, sel=np.sort(rng.choice(scene.n, min(m, 256), replace=False)))
+    times = []
+    for _ in range(args.steps):
+        sel = np.sort(rng.choice(scene.n, m, replace=False))
+        t0 = time.perf_counter()
+        oracle.step(scene, sel=sel)
+        times.append(time.perf_counter() - t0)
+    value = m * args.steps / sum(times)
+    sample = (f"{m} agents drawn per step from the {cfg['agents']}-agent workload, "
+              f"FP64 oracle (brute-force neighbours), {args.steps} steps from the initial state")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step_sample": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(scene, cfg, budget_s=12.0):
+    """Oracle timed on a bounded sample of the same workload (rank 0, N=1)."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(1)
+    probe = np.sort(rng.choice(scene.n, min(scene.n, 200), replace=False))
+    t0 = time.perf_counter()
+    oracle.step(scene, sel=probe)
+    per_agent = (time.perf_counter() - t0) / len(probe)
+    m = int(min(scene.n, max(100, budget_s / max(per_agent, 1e-9))))
+    sel = np.sort(rng.choice(scene.n, m, replace=False))
+    t0 = time.perf_counter()
+    oracle.step(scene, sel=sel)
+    dt = time.perf_counter() - t0
+    return {"value": m / dt, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one step of {m} agents drawn from the {cfg['agents']}-agent workload "
+                      f"({dt:.1f} s, FP64, brute-force neighbours)"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2008_11578_gb300 import api, build
+
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build()
+    scene, cfg = _scene(args.workload)
+    n = scene.n
+    ds = api.DeviceScene(scene, dev, cell_size=args.cell_size)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        ds.step(1)
+    torch.cuda.synchronize()
+    assert ds.sync_status() == 0, "non-finite state after warm-up"
+
+    # ---- timed region: K steps, device-resident state ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    sv = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] \
+        if "CUDA_VISIBLE_DEVICES" in os.environ else local
+    barrier()
+    with ClockSampler(gpu_index) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            api.orca_scene_set_solve_events(ds.handle, sv[k][0], sv[k][1])
+            ev[k][0].record(stream)
+            ds.step(1)
+            ev[k][1].record(stream)
+        barrier()
+    api.orca_scene_set_solve_events(ds.handle, None, None)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    solve_ms = [a.elapsed_time(b) for a, b in sv]
+    total_s = sum(step_ms) / 1e3
+    t = torch.tensor([total_s], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_max = float(t.item())
+    value = n * args.steps * world / total_max
+    clocks = clk.summary()
+
+    # ---- algorithmic FLOPs of the solve kernel (untimed counting step) ----
+    counters = torch.zeros(5, dtype=torch.int64, device=dev)
+    saved = (ds.pos.clone(), ds.vel.clone())
+    api.orca_scene_set_counters(ds.handle, counters)
+    ds.step(1)
+    api.orca_scene_set_counters(ds.handle, None)
+    ds.pos.copy_(saved[0])
+    ds.vel.copy_(saved[1])
+    c = counters.cpu().numpy().astype(np.float64)
+    flops = FLOPS_CAND * c[0] + FLOPS_LINE * c[1] + FLOPS_PAIR * c[2] + FLOPS_AGENT * c[4]
+    solve_avg_s = statistics.mean(solve_ms) / 1e3
+    peak_tflops = 2 * FP32_LANES * SMS * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops / solve_avg_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": "solve_kernel", "solve_ms": statistics.mean(solve_ms),
+                "solve_share_of_step": statistics.mean(solve_ms) / statistics.mean(step_ms),
+                "flops_per_agent_step": flops / n,
+                "counts_per_agent": {"candidates": c[0] / n, "neighbours": c[1] / n,
+                                     "lp_pairs": c[2] / n, "fallback_frac": c[3] / n},
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz (nominal max clock)"}
+
+    # ---- end to end through the public API from pinned host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.empty((n, 2), dtype=torch.float32, pin_memory=True)
+        hv = torch.empty((n, 2), dtype=torch.float32, pin_memory=True)
+        op = torch.empty((n, 2), dtype=torch.float32, pin_memory=True)
+        ov = torch.empty((n, 2), dtype=torch.float32, pin_memory=True)
+        hp.copy_(ds.pos)
+        hv.copy_(ds.vel)
+        eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        barrier()
+        for k in range(args.steps):
+            flush.zero_()
+            eev[k][0].record(stream)
+            ds.pos.copy_(hp, non_blocking=True)
+            ds.vel.copy_(hv, non_blocking=True)
+            ds.step(1)
+            op.copy_(ds.pos, non_blocking=True)
+            ov.copy_(ds.vel, non_blocking=True)
+            eev[k][1].record(stream)
+        barrier()
+        e_total = sum(a.elapsed_time(b) for a, b in eev) / 1e3
+        te = torch.tensor([e_total], device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": n * args.steps * world / float(te.item()), "unit": METRIC,
+               "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 2 * 8 * n}
+
+    status = ds.sync_status()
+    peaks = _peaks()
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": dict(cfg, l2="flushed before every timed step (256 MB write)",
+                           parallelism=f"replicas{world}" if world > 1 else "single",
+                           cell_size_m=float(ds.params.cell_size),
+                           neighbor_dist_m=10.0, max_neighbors=10, tau_s=5.0, dt_s=0.25),
+            "clocks": clocks, "gpu_launches": ds.launch_count(1) * args.steps,
+            "roofline": roofline, "e2e": e2e, "status": status,
+            "hbm_peak_gbs": peaks.get("hbm_gbs")}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(scene, cfg)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ds.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="clusters_1m")
+    ap.add_argument("--cell-size", type=float, default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

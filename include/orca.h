@@ -1,0 +1,205 @@
+/*
+ * orca.h -- C ABI of liborca, the GB300 (sm_103a) implementation of the
+ * per-time-step ORCA update for pedestrians and autonomous vehicles
+ * (Charlton et al., "Simulating Crowds and Autonomous Vehicles").
+ *
+ * One step moves every agent once, all agents reading the state of step t
+ * (paper Sec. 3, overview paragraph):
+ *   1. bin agents into a uniform grid (Sec. 1, grid-partitioned messaging);
+ *   2. each agent observes the radius, position and velocity of its k
+ *      nearest neighbours within the neighbour distance (Sec. 3);
+ *   3. one ORCA half-plane per neighbour, placed at v_opt + f_{A|B} u with
+ *      the responsibility factor of the ordered pair of agent types
+ *      (Sec. 3.1, Fig. 1c);
+ *   4. the admissible velocity closest to the preferred velocity (Sec. 3,
+ *      LP paragraphs); when no velocity is admissible, the velocity of least
+ *      penetration (Sec. 3, infeasible-set paragraph);
+ *   5. position update with the new velocity.
+ *
+ * Conventions shared by every entry point
+ *   - All agent arrays are DEVICE memory owned by the caller, in the
+ *     caller's agent order.  Arrays of 2D vectors are interleaved (x, y)
+ *     float pairs ("float2"), 8-byte aligned.  The library keeps non-owning
+ *     pointers to them; they must outlive the scene.
+ *   - The workspace is device memory owned by the caller, at least
+ *     orca_workspace_bytes() bytes, 256-byte aligned.  The library never
+ *     allocates device memory in a step.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Calls that take a stream are asynchronous on it.
+ *   - Every function returns an int status (ORCA_OK = 0).  Nothing throws.
+ *     Argument errors are detected on the host before any launch.  Errors
+ *     raised inside kernels (non-finite inputs, a bounded wait that gave up)
+ *     are recorded in a device error word that orca_scene_sync_status()
+ *     reads and clears.
+ *   - Agent types: 0 = pedestrian, 1 = vehicle.  Both run the same code;
+ *     only radius, max speed and the f table entries differ (Sec. 3.1).
+ */
+#ifndef ORCA_H_
+#define ORCA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORCA_OK 0
+#define ORCA_ERR_INVALID_ARG 1   /* bad pointer, size, parameter or alignment */
+#define ORCA_ERR_CUDA 2          /* a CUDA runtime call or launch failed */
+#define ORCA_ERR_TIMEOUT 3       /* a bounded device wait gave up */
+#define ORCA_ERR_NONFINITE 4     /* a position or velocity was NaN/Inf */
+#define ORCA_ERR_CAPACITY 5      /* k above ORCA_MAX_NEIGHBORS, grid too large */
+
+/* largest max_neighbors the kernels are compiled for */
+#define ORCA_MAX_NEIGHBORS 32
+/* largest number of grid cells of one scene */
+#define ORCA_MAX_CELLS (1 << 26)
+
+/* debug_flags bits */
+#define ORCA_DEBUG_NONE 0u
+
+/*
+ * Global parameters of one scene (Sec. 3 and 3.1).
+ *   neighbor_dist   R_n: agents closer than this are neighbour candidates
+ *   time_horizon    tau: look-ahead of the velocity obstacles, seconds
+ *   dt              step length, seconds
+ *   max_neighbors   k: the k nearest candidates become constraints
+ *                   (0 <= k <= ORCA_MAX_NEIGHBORS)
+ *   f[a][b]         responsibility factor f_{A|B} of an agent of type a
+ *                   avoiding one of type b (paper default 1/2, 1, 0, 1/2)
+ *   cell_size       grid cell edge; any positive value gives identical
+ *                   results (the neighbour search is exact), only speed
+ *                   changes
+ *   origin_x/y, grid_nx/ny   grid box; agents outside clamp to edge cells
+ *   block_size      threads per block of the solve kernel (0 = 128)
+ *   debug_flags     ORCA_DEBUG_* bits (0)
+ */
+typedef struct orca_params {
+    float neighbor_dist;
+    float time_horizon;
+    float dt;
+    int max_neighbors;
+    float f[2][2];
+    float cell_size;
+    float origin_x;
+    float origin_y;
+    int grid_nx;
+    int grid_ny;
+    int block_size;
+    unsigned debug_flags;
+} orca_params;
+
+/*
+ * Agents of one scene (Sec. 3: start, goal, radius, speeds).  Device
+ * pointers, caller's order, N = n_agents.
+ *   pos, vel        float2[N], read at step start, written at the end
+ *   goal            float2[N]
+ *   radius          float[N]  (> 0)
+ *   max_speed       float[N]  (>= 0); the preferred velocity points at the
+ *                   goal with this speed, capped so as not to overshoot
+ *   type            uint8[N]  (0 pedestrian, 1 vehicle)
+ *   route           int32[N] or NULL: row of `waypoints` the agent follows,
+ *                   -1 = follow `goal`
+ *   waypoints       float2[n_routes * n_waypoints] (row-major), or NULL
+ *   wp_idx          uint8[N] current waypoint of each agent, read and
+ *                   written by every step; required when route != NULL
+ */
+typedef struct orca_agents {
+    int n_agents;
+    float *pos;
+    float *vel;
+    const float *goal;
+    const float *radius;
+    const float *max_speed;
+    const uint8_t *type;
+    const int32_t *route;
+    const float *waypoints;
+    int n_routes;
+    int n_waypoints;
+    uint8_t *wp_idx;
+} orca_agents;
+
+typedef struct orca_scene orca_scene;
+typedef struct orca_batch orca_batch;
+
+/* Human-readable name of a status code (static string). */
+const char *orca_status_string(int status);
+
+/* ABI version of this header (increments on any signature change). */
+int orca_abi_version(void);
+
+/*
+ * Workspace bytes a scene of n_agents agents with these parameters needs.
+ * Returns ORCA_ERR_INVALID_ARG / ORCA_ERR_CAPACITY on bad parameters.
+ */
+int orca_workspace_bytes(const orca_params *params, int n_agents, size_t *out_bytes);
+
+/*
+ * Create a scene over caller-owned agent arrays and workspace.  Validates
+ * everything that can be checked on the host (sizes, alignment, parameter
+ * ranges) and launches nothing.  *out receives a host object that
+ * orca_scene_destroy() frees.
+ */
+int orca_scene_create(const orca_params *params, const orca_agents *agents,
+                      void *workspace, size_t workspace_bytes, orca_scene **out);
+
+/*
+ * Optional per-agent diagnostics written by every following step (for the
+ * last step of a call), caller's order; any pointer may be NULL:
+ *   cell[N]        int32 grid cell id cy * nx + cx of the agent at step start
+ *   nbr[N * k]     int32 neighbour indices in constraint order, -1 padded
+ *   cnt[N]         int32 number of neighbours
+ *   flags[N]       uint8 bit0 = half-planes infeasible (least-penetration
+ *                  fallback taken), bit2 = overlaps a neighbour
+ *   tstar[N]       float least penetration t* (only for bit0 agents, else 0)
+ */
+int orca_scene_set_debug(orca_scene *scene, int32_t *cell, int32_t *nbr,
+                         int32_t *cnt, uint8_t *flags, float *tstar);
+
+/*
+ * Advance the scene n_steps synchronous steps (n_steps >= 0).  pos, vel and
+ * wp_idx are updated in place.  vpref_delta is NULL or float2[n_steps * N]:
+ * an offset added to the preferred velocity of agent i at step t at
+ * vpref_delta[t * N + i] (the leaf of the adjoint).
+ */
+int orca_step(orca_scene *scene, int n_steps, const float *vpref_delta, void *stream);
+
+/*
+ * Record two caller-created CUDA events (cudaEvent_t passed as void*, or
+ * NULL to stop) on the step's stream right before and right after the solve
+ * kernel of every following step, so a caller can time that kernel alone.
+ * With n_steps > 1 the events bracket the last step's solve kernel.
+ */
+int orca_scene_set_solve_events(orca_scene *scene, void *begin, void *end);
+
+/*
+ * Work tallies for FLOP accounting, or NULL to stop.  counters is device
+ * memory, uint64[5], accumulated (never cleared) by every following step:
+ *   [0] candidate key tests of the neighbour search
+ *   [1] ORCA half-planes built
+ *   [2] LP pair evaluations (a constraint tested against another inside a
+ *       1D sub-problem or a bisector sub-problem)
+ *   [3] agents whose half-planes were infeasible
+ *   [4] agent updates
+ * A scene with counters set runs a separate, slower kernel variant.
+ */
+int orca_scene_set_counters(orca_scene *scene, unsigned long long *counters);
+
+/* Number of kernel launches one orca_step call of n_steps makes. */
+int orca_step_launch_count(const orca_scene *scene, int n_steps);
+
+/*
+ * Synchronise the device, then read and clear the scene's device error
+ * word.  Returns ORCA_OK or the first recorded error status.
+ */
+int orca_scene_sync_status(orca_scene *scene);
+
+/* Free the host object (the caller's device memory is untouched). */
+void orca_scene_destroy(orca_scene *scene);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ORCA_H_ */

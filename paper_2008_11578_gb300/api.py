@@ -1,0 +1,210 @@
+"""Python binding of liborca: argument marshalling only.
+
+Functions named like the C entry points (``orca_workspace_bytes``,
+``orca_scene_create``, ``orca_step`` ...) forward to the C ABI with device
+pointers taken from torch tensors; :class:`DeviceScene` bundles the tensors
+of one scene.  Every step of the ORCA update runs in liborca's kernels;
+torch provides device memory and the current stream only.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+
+from . import _lib
+from ._lib import OrcaAgents, OrcaError, OrcaParams, check
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_params(p, cell_size: float | None = None, block_size: int = 0) -> OrcaParams:
+    """orca_params from a :class:`scenes.OrcaParams` (grid from its box)."""
+    c = float(p.cell_size if cell_size is None else cell_size)
+    nx, ny = p.grid_dims(c)
+    f = np.asarray(p.f, dtype=np.float32).reshape(2, 2)
+    cp = OrcaParams()
+    cp.neighbor_dist = float(p.neighbor_dist)
+    cp.time_horizon = float(p.time_horizon)
+    cp.dt = float(p.dt)
+    cp.max_neighbors = int(p.max_neighbors)
+    for a in range(2):
+        for b in range(2):
+            cp.f[a][b] = float(f[a, b])
+    cp.cell_size = c
+    cp.origin_x = float(p.origin[0])
+    cp.origin_y = float(p.origin[1])
+    cp.grid_nx = int(nx)
+    cp.grid_ny = int(ny)
+    cp.block_size = int(block_size)
+    cp.debug_flags = 0
+    return cp
+
+
+# ------------------------------------------------------------- C names ------
+
+def orca_status_string(status: int) -> str:
+    return _lib.load().orca_status_string(int(status)).decode()
+
+
+def orca_abi_version() -> int:
+    return int(_lib.load().orca_abi_version())
+
+
+def orca_workspace_bytes(params: OrcaParams, n_agents: int) -> int:
+    out = ctypes.c_size_t(0)
+    check(_lib.load().orca_workspace_bytes(ctypes.byref(params), int(n_agents),
+                                           ctypes.byref(out)), "orca_workspace_bytes")
+    return int(out.value)
+
+
+def orca_scene_create(params: OrcaParams, agents: OrcaAgents, workspace, ws_bytes: int):
+    h = ctypes.c_void_p()
+    check(_lib.load().orca_scene_create(ctypes.byref(params), ctypes.byref(agents),
+                                        _ptr(workspace), int(ws_bytes), ctypes.byref(h)),
+          "orca_scene_create")
+    return h
+
+
+def orca_scene_set_debug(handle, cell=None, nbr=None, cnt=None, flags=None, tstar=None):
+    check(_lib.load().orca_scene_set_debug(handle, _ptr(cell), _ptr(nbr), _ptr(cnt),
+                                           _ptr(flags), _ptr(tstar)), "orca_scene_set_debug")
+
+
+def orca_scene_set_solve_events(handle, begin=None, end=None):
+    """Bracket the solve kernel of every following step with two
+    ``torch.cuda.Event(enable_timing=True)`` (or None to stop)."""
+    b = None if begin is None else ctypes.c_void_p(begin.cuda_event)
+    e = None if end is None else ctypes.c_void_p(end.cuda_event)
+    check(_lib.load().orca_scene_set_solve_events(handle, b, e), "orca_scene_set_solve_events")
+
+
+def orca_scene_set_counters(handle, counters=None):
+    """Accumulate work tallies into ``counters`` (int64[5] on the device)."""
+    check(_lib.load().orca_scene_set_counters(handle, _ptr(counters)), "orca_scene_set_counters")
+
+
+def orca_step(handle, n_steps: int, vpref_delta=None, stream=None):
+    check(_lib.load().orca_step(handle, int(n_steps), _ptr(vpref_delta),
+                                _stream_handle(stream)), "orca_step")
+
+
+def orca_step_launch_count(handle, n_steps: int) -> int:
+    return int(_lib.load().orca_step_launch_count(handle, int(n_steps)))
+
+
+def orca_scene_sync_status(handle) -> int:
+    return int(_lib.load().orca_scene_sync_status(handle))
+
+
+def orca_scene_destroy(handle) -> None:
+    _lib.load().orca_scene_destroy(handle)
+
+
+# ------------------------------------------------------------- scene --------
+
+class DeviceScene:
+    """One scene's agent arrays and workspace on the GPU, behind liborca.
+
+    ``scene`` is a :class:`scenes.Scene` (numpy, caller order).  The device
+    tensors ``pos``, ``vel`` and ``wp_idx`` are updated in place by
+    :meth:`step`; ``goal``, ``radius``, ``max_speed``, ``type``, ``route``
+    and ``waypoints`` are read-only inputs.
+    """
+
+    def __init__(self, scene, device="cuda", cell_size=None, block_size=0, debug=False):
+        torch = _torch()
+        self.device = torch.device(device)
+        self.scene = scene
+        self.n = scene.n
+        self.k = int(scene.params.max_neighbors)
+        dev = self.device
+
+        def t(a, dt=None):
+            return torch.as_tensor(np.ascontiguousarray(a), device=dev, dtype=dt)
+
+        self.pos = t(scene.pos, torch.float32)
+        self.vel = t(scene.vel, torch.float32)
+        self.goal = t(scene.goal, torch.float32)
+        self.radius = t(scene.radius, torch.float32)
+        self.max_speed = t(scene.max_speed, torch.float32)
+        self.type = t(scene.type, torch.uint8)
+        self.route = self.waypoints = self.wp_idx = None
+        if scene.route is not None:
+            self.route = t(scene.route, torch.int32)
+            self.waypoints = t(scene.waypoints.reshape(-1, 2), torch.float32)
+            self.wp_idx = t(scene.wp_idx, torch.uint8)
+        self.params = make_params(scene.params, cell_size, block_size)
+        self.ws_bytes = orca_workspace_bytes(self.params, self.n)
+        self.workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
+        a = OrcaAgents()
+        a.n_agents = self.n
+        a.pos, a.vel, a.goal = _ptr(self.pos), _ptr(self.vel), _ptr(self.goal)
+        a.radius, a.max_speed, a.type = _ptr(self.radius), _ptr(self.max_speed), _ptr(self.type)
+        a.route = _ptr(self.route)
+        a.waypoints = _ptr(self.waypoints)
+        a.n_routes = 0 if scene.route is None else int(scene.waypoints.shape[0])
+        a.n_waypoints = 0 if scene.route is None else int(scene.waypoints.shape[1])
+        a.wp_idx = _ptr(self.wp_idx)
+        self._agents = a
+        self.handle = orca_scene_create(self.params, a, self.workspace, self.ws_bytes)
+        self.dbg = None
+        if debug:
+            self.enable_debug()
+
+    def enable_debug(self):
+        torch = _torch()
+        n, k, dev = self.n, max(self.k, 1), self.device
+        self.dbg = dict(cell=torch.full((n,), -1, dtype=torch.int32, device=dev),
+                        nbr=torch.full((n, k), -1, dtype=torch.int32, device=dev),
+                        cnt=torch.zeros(n, dtype=torch.int32, device=dev),
+                        flags=torch.zeros(n, dtype=torch.uint8, device=dev),
+                        tstar=torch.zeros(n, dtype=torch.float32, device=dev))
+        orca_scene_set_debug(self.handle, **self.dbg)
+
+    def set_state(self, pos=None, vel=None, wp_idx=None):
+        torch = _torch()
+        if pos is not None:
+            self.pos.copy_(torch.as_tensor(pos, dtype=torch.float32))
+        if vel is not None:
+            self.vel.copy_(torch.as_tensor(vel, dtype=torch.float32))
+        if wp_idx is not None and self.wp_idx is not None:
+            self.wp_idx.copy_(torch.as_tensor(wp_idx, dtype=torch.uint8))
+
+    def step(self, n_steps: int = 1, vpref_delta=None, stream=None):
+        if vpref_delta is not None:
+            assert vpref_delta.dtype == _torch().float32 and vpref_delta.is_contiguous()
+            assert vpref_delta.numel() == 2 * n_steps * self.n
+        orca_step(self.handle, n_steps, vpref_delta, stream)
+
+    def launch_count(self, n_steps: int) -> int:
+        return orca_step_launch_count(self.handle, n_steps)
+
+    def sync_status(self) -> int:
+        return orca_scene_sync_status(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            orca_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,85 @@
+// orca_kernels.cuh -- kernels of one ORCA step over one or many scenes.
+//
+// Data layout (device, structure of arrays):
+//   caller order     user pos/vel/goal/radius/max_speed/type/route/wp_idx
+//   "state" order    pos0/vel0: output of the solve kernel, in the cell order
+//                    of the step that produced it (caller order right after
+//                    the load kernel)
+//   sorted order     pos1/vel1 + rad/typ/orig: agents grouped by grid cell,
+//                    cells in row-major order, scenes one after another
+// One step: bin_count (key + per-cell slot) -> 3-phase exclusive scan of the
+// cell counts -> scatter into sorted order -> solve (one thread per agent:
+// k-nearest ring search, ORCA lines, LP, integrate) writing pos0/vel0 in
+// sorted order, which becomes the state order of the next step.
+#pragma once
+
+#include <climits>
+
+#include "orca_math.cuh"
+
+namespace orca {
+
+// per-scene constants
+struct SceneDev {
+    int agent_off;     // first sorted slot of the scene
+    int n_agents;
+    int cell_off;      // first global cell of the scene
+    int nx, ny;
+    float origin_x, origin_y;
+    float inv_cell;    // fl32(1 / cell_size)
+    float cell_size;
+    float ring_delta;  // cell-rounding margin of the ring search, in cells
+    float R2;          // fl32(R_n * R_n)
+    int k;
+    float inv_tau, inv_dt, dt;
+    float f00, f01, f10, f11;
+};
+
+struct OneScene {
+    SceneDev s;
+    __device__ __forceinline__ const SceneDev& get(int) const { return s; }
+};
+
+struct ManyScenes {
+    const SceneDev* __restrict__ s;
+    const int* __restrict__ sid;   // scene of every sorted slot (fixed)
+    __device__ __forceinline__ SceneDev get(int i) const { return s[__ldg(sid + i)]; }
+};
+
+// caller-order per-agent inputs of the solve kernel
+struct AgentIn {
+    const float2* __restrict__ goal;
+    const float* __restrict__ max_speed;
+    const int32_t* __restrict__ route;     // may be null
+    const float2* __restrict__ waypoints;
+    int n_waypoints;
+    uint8_t* __restrict__ wp_idx;          // may be null when route is null
+};
+
+struct DebugOut {
+    int32_t* cell;
+    int32_t* nbr;
+    int32_t* cnt;
+    uint8_t* flags;
+    float* tstar;
+    int k_stride;
+};
+
+// Work tallies of the counting variant of the solve kernel:
+// [0] candidate key tests, [1] ORCA lines built, [2] LP pair evaluations
+// (one constraint against another inside a 1D or bisector sub-problem),
+// [3] agents that took the least-penetration fallback, [4] agents.
+constexpr int kNumCounters = 5;
+
+enum : int { ERR_BIT_NONFINITE = 1, ERR_BIT_TIMEOUT = 2 };
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kScanThreads * kScanItems;   // cells per scan block
+
+// Slack and tolerance of the relaxed tie-break projection after the
+// least-penetration LP (absolute, m/s).
+constexpr float kTieSlack = 0.0f;
+constexpr float kTieTol = 1e-3f;
+
+}  // namespace orca

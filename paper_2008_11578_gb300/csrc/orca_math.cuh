@@ -1,0 +1,283 @@
+// orca_math.cuh -- per-agent device math of the ORCA step (FP32).
+//
+// Discrete decisions (cell, neighbour key, overlap, waypoint advance, leg
+// side) use explicitly rounded intrinsics in a fixed order so that they
+// never get contracted into FMAs: they are part of the specification both
+// implementations evaluate identically.  Everything else is plain FP32.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+namespace orca {
+
+// Cell along one axis: clamp(floor(fl32(fl32(x - o) * inv)), 0, n - 1).
+__device__ __forceinline__ int cell_axis(float x, float o, float inv, int n) {
+    float t = __fmul_rn(__fsub_rn(x, o), inv);
+    float fl = floorf(t);
+    if (!(fl >= 0.0f)) return 0;
+    if (fl >= (float)(n - 1)) return n - 1;
+    return (int)fl;
+}
+
+// Neighbour key d^2 = fl32(fl32(dx*dx) + fl32(dy*dy)), dx = fl32(xb - xa).
+__device__ __forceinline__ float key_d2(float xa, float ya, float xb, float yb) {
+    float dx = __fsub_rn(xb, xa);
+    float dy = __fsub_rn(yb, ya);
+    return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+}
+
+// Which leg of the velocity obstacle is closer: det(q, w_rel) > 0 means the
+// left leg (ties go right).  The decision is defined by the FP64 evaluation
+// q = p_B - p_A, w = v_A - v_B, det = q_x w_y - q_y w_x (no contraction).  An
+// FP32 filter with a rigorous error bound settles almost every pair; only
+// near-zero determinants pay for the FP64 evaluation.
+__device__ __forceinline__ bool leg_left(float pax, float pay, float pbx, float pby,
+                                         float vax, float vay, float vbx, float vby) {
+    float qx = __fsub_rn(pbx, pax), qy = __fsub_rn(pby, pay);
+    float wx = __fsub_rn(vax, vbx), wy = __fsub_rn(vay, vby);
+    float a = __fmul_rn(qx, wy), b = __fmul_rn(qy, wx);
+    float det = __fsub_rn(a, b);
+    // |det32 - det_exact| <= ~4u (|a| + |b|); 10u leaves margin
+    float bound = 5.97e-7f * (fabsf(a) + fabsf(b));
+    if (fabsf(det) > bound) return det > 0.0f;
+    double qx64 = __dsub_rn((double)pbx, (double)pax);
+    double qy64 = __dsub_rn((double)pby, (double)pay);
+    double wx64 = __dsub_rn((double)vax, (double)vbx);
+    double wy64 = __dsub_rn((double)vay, (double)vby);
+    double d64 = __dsub_rn(__dmul_rn(qx64, wy64), __dmul_rn(qy64, wx64));
+    return d64 > 0.0;
+}
+
+// ORCA half-plane of agent A against neighbour B (paper Sec. 3.1, Fig. 1).
+// q = p_B - p_A, w_rel = v_A - v_B, rho = r_A + r_B.  The velocity obstacle is
+// the cone from the origin tangent to D(q/tau, rho/tau), cut off by that
+// disc; u runs from w_rel to its closest boundary point.  Overlapping pairs
+// use the cut-off construction with tau replaced by dt.  The line passes
+// through v_A + f u; its admissible side is left of the unit direction d.
+// Returned as (P_x, P_y, d_x, d_y).
+__device__ __forceinline__ float4 orca_line(float pax, float pay, float vax, float vay,
+                                            float ra, float pbx, float pby, float vbx,
+                                            float vby, float rb, float f, float inv_tau,
+                                            float inv_dt, bool overlap) {
+    float qx = pbx - pax, qy = pby - pay;
+    float wrx = vax - vbx, wry = vay - vby;
+    float rho = ra + rb;
+    float ux, uy, dx, dy;
+    if (!overlap) {
+        float wx = wrx - qx * inv_tau, wy = wry - qy * inv_tau;
+        float wq = wx * qx + wy * qy;
+        float ww = wx * wx + wy * wy;
+        float rho2 = rho * rho;
+        if (wq < 0.0f && wq * wq > rho2 * ww) {
+            // cut-off circle
+            float wl = sqrtf(ww);
+            float hx = wx / wl, hy = wy / wl;
+            dx = hy;
+            dy = -hx;
+            float s = rho * inv_tau - wl;
+            ux = s * hx;
+            uy = s * hy;
+        } else {
+            // legs
+            float qq = qx * qx + qy * qy;
+            float l = sqrtf(fmaxf(qq - rho2, 0.0f));
+            bool left = leg_left(pax, pay, pbx, pby, vax, vay, vbx, vby);
+            float iq = 1.0f / qq;
+            if (left) {
+                dx = (qx * l - qy * rho) * iq;
+                dy = (qx * rho + qy * l) * iq;
+            } else {
+                dx = -(qx * l + qy * rho) * iq;
+                dy = -(qy * l - qx * rho) * iq;
+            }
+            float pr = wrx * dx + wry * dy;
+            ux = pr * dx - wrx;
+            uy = pr * dy - wry;
+        }
+    } else {
+        float wx = wrx - qx * inv_dt, wy = wry - qy * inv_dt;
+        float wl = sqrtf(wx * wx + wy * wy);
+        float hx, hy;
+        if (wl > 0.0f) {
+            hx = wx / wl;
+            hy = wy / wl;
+        } else {
+            float ql = sqrtf(qx * qx + qy * qy);
+            if (ql > 0.0f) {
+                hx = -qx / ql;
+                hy = -qy / ql;
+            } else {
+                hx = -1.0f;
+                hy = 0.0f;
+            }
+        }
+        dx = hy;
+        dy = -hx;
+        float s = rho * inv_dt - wl;
+        ux = s * hx;
+        uy = s * hy;
+    }
+    return make_float4(vax + f * ux, vay + f * uy, dx, dy);
+}
+
+// det(d, P - v): positive = v violates the half-plane
+__device__ __forceinline__ float penetration(float4 L, float vx, float vy) {
+    return L.z * (L.y - vy) - L.w * (L.x - vx);
+}
+
+// ---------------------------------------------------------------------------
+// Velocity LP (paper Sec. 3, LP paragraphs).  Lines live in shared memory at
+// L[i * stride].  The objective is the Euclidean distance to v_pref, so the
+// incremental scheme is exact: when the current optimum violates line i, the
+// new optimum lies on line i, and a 1D problem on that line with the earlier
+// lines and the speed disc finds it.
+// ---------------------------------------------------------------------------
+
+// 1D problem on line i.  tol > 0 accepts intervals that are empty by at most
+// tol (rounding in the relaxed tie-break problem) and takes their midpoint.
+__device__ __forceinline__ bool lp1_project(const float4* __restrict__ L, int stride, int i,
+                                            float vmax, float vpx, float vpy, float tol,
+                                            float& ox, float& oy, int& work) {
+    float4 li = L[i * stride];
+    float dot = li.x * li.z + li.y * li.w;
+    float disc = dot * dot + vmax * vmax - (li.x * li.x + li.y * li.y);
+    if (disc < 0.0f) {
+        if (disc < -tol * (1.0f + vmax * vmax)) return false;
+        disc = 0.0f;
+    }
+    float sq = sqrtf(disc);
+    float tl = -dot - sq, tr = -dot + sq;
+    for (int j = 0; j < i; ++j) {
+        ++work;
+        float4 lj = L[j * stride];
+        float den = li.z * lj.w - li.w * lj.z;                     // det(d_i, d_j)
+        float num = lj.z * (li.y - lj.y) - lj.w * (li.x - lj.x);   // det(d_j, P_i - P_j)
+        if (den == 0.0f) {
+            if (num < -tol) return false;
+            continue;
+        }
+        float t = num / den;
+        if (den > 0.0f) tr = fminf(tr, t);
+        else tl = fmaxf(tl, t);
+        if (tl > tr + tol) return false;
+    }
+    if (tl > tr) {
+        float m = 0.5f * (tl + tr);
+        tl = m;
+        tr = m;
+    }
+    float t = li.z * (vpx - li.x) + li.w * (vpy - li.y);
+    t = fminf(fmaxf(t, tl), tr);
+    ox = li.x + t * li.z;
+    oy = li.y + t * li.w;
+    return true;
+}
+
+// Projection of v_pref onto the half-planes and the disc.  Returns n on
+// success, else the index of the line whose 1D problem was empty (v keeps
+// the optimum of the lines before it).
+__device__ __forceinline__ int lp2_project(const float4* __restrict__ L, int stride, int n,
+                                           float vmax, float vpx, float vpy, float tol,
+                                           float& vx, float& vy, int& work) {
+    float vp2 = vpx * vpx + vpy * vpy;
+    if (vp2 > vmax * vmax) {
+        float s = vmax / sqrtf(vp2);
+        vx = vpx * s;
+        vy = vpy * s;
+    } else {
+        vx = vpx;
+        vy = vpy;
+    }
+    for (int i = 0; i < n; ++i) {
+        float4 li = L[i * stride];
+        if (penetration(li, vx, vy) > 0.0f) {
+            float ox, oy;
+            if (!lp1_project(L, stride, i, vmax, vpx, vpy, tol, ox, oy, work)) return i;
+            vx = ox;
+            vy = oy;
+        }
+    }
+    return n;
+}
+
+// Boundary of {v : det_j(v) <= det_i(v)} as a line with its admissible side
+// on the left: direction (d_j - d_i) normalised, through the intersection of
+// lines i and j; for opposite parallel lines the mid-line.  Returns false for
+// same-direction parallel lines (one of them dominates everywhere).
+__device__ __forceinline__ bool bisector(float4 li, float4 lj, float4& b) {
+    float det = li.z * lj.w - li.w * lj.z;
+    float ex = lj.z - li.z, ey = lj.w - li.w;
+    float el2 = ex * ex + ey * ey;
+    if (fabsf(det) <= 1e-6f) {
+        if (li.z * lj.z + li.w * lj.w > 0.0f) return false;
+        float inv = rsqrtf(el2);
+        b = make_float4(0.5f * (li.x + lj.x), 0.5f * (li.y + lj.y), ex * inv, ey * inv);
+        return true;
+    }
+    // X = P_i + s d_i with s = det(d_j, P_j - P_i) / det(d_j, d_i)
+    float s = (lj.z * (lj.y - li.y) - lj.w * (lj.x - li.x)) / (-det);
+    float inv = rsqrtf(el2);
+    b = make_float4(li.x + s * li.z, li.y + s * li.w, ex * inv, ey * inv);
+    return true;
+}
+
+// Least penetration (paper Sec. 3, infeasible-set paragraph):
+// t* = min over |v| <= vmax of max_i det(d_i, P_i - v), by the incremental
+// LP in (v, t): when the optimum violates plane i, the new optimum lies on
+// it, where minimising det_i(v) subject to det_j(v) <= det_i(v) (j < i) and
+// the disc is a 2D LP with the linear objective n_i . v.  Writes the point.
+__device__ __forceinline__ float lp3_min_penetration(const float4* __restrict__ L, int stride,
+                                                     int n, float vmax, float& vx, float& vy,
+                                                     int& work) {
+    float4 l0 = L[0];
+    vx = -l0.w * vmax;
+    vy = l0.z * vmax;
+    float t = penetration(l0, vx, vy);
+    for (int i = 1; i < n; ++i) {
+        float4 li = L[i * stride];
+        if (penetration(li, vx, vy) <= t) continue;
+        float nix = -li.w, niy = li.z;   // objective: maximise n_i . v
+        float cx = vmax * nix, cy = vmax * niy;
+        for (int j = 0; j < i; ++j) {
+            ++work;
+            float4 bj;
+            if (!bisector(li, L[j * stride], bj)) continue;
+            if (penetration(bj, cx, cy) <= 0.0f) continue;
+            float dot = bj.x * bj.z + bj.y * bj.w;
+            float disc = dot * dot + vmax * vmax - (bj.x * bj.x + bj.y * bj.y);
+            if (disc < 0.0f) continue;
+            float sq = sqrtf(disc);
+            float tl = -dot - sq, tr = -dot + sq;
+            bool ok = true;
+            for (int jj = 0; jj < j; ++jj) {
+                work += 2;   // a bisector and a 1D bound
+                float4 bk;
+                if (!bisector(li, L[jj * stride], bk)) continue;
+                float den = bj.z * bk.w - bj.w * bk.z;
+                float num = bk.z * (bj.y - bk.y) - bk.w * (bj.x - bk.x);
+                if (den == 0.0f) {
+                    if (num < 0.0f) { ok = false; break; }
+                    continue;
+                }
+                float tt = num / den;
+                if (den > 0.0f) tr = fminf(tr, tt);
+                else tl = fmaxf(tl, tt);
+                if (tl > tr) { ok = false; break; }
+            }
+            if (!ok) continue;   // empty only through rounding: keep the point
+            float tt = (nix * bj.z + niy * bj.w > 0.0f) ? tr : tl;
+            cx = bj.x + tt * bj.z;
+            cy = bj.y + tt * bj.w;
+        }
+        vx = cx;
+        vy = cy;
+        t = penetration(li, vx, vy);
+    }
+    float tm = -CUDART_INF_F;
+    for (int i = 0; i < n; ++i) tm = fmaxf(tm, penetration(L[i * stride], vx, vy));
+    return tm;
+}
+
+}  // namespace orca

@@ -1,0 +1,396 @@
+// orca_step_kernels.cuh -- device kernels of the ORCA step (sm_103a).
+//
+// Memory-bound kernels (load, bin_count, scan, scatter, unload) are one
+// thread per element with coalesced accesses; the solve kernel is one thread
+// per agent in cell-sorted order, so the 32 agents of a warp come from a few
+// neighbouring cells and read the same candidate cells through L1.
+#pragma once
+
+#include "orca_kernels.cuh"
+
+namespace orca {
+
+// ------------------------------------------------------------------ load ----
+__global__ void load_kernel(int n, const float2* __restrict__ upos,
+                            const float2* __restrict__ uvel,
+                            const float* __restrict__ uradius,
+                            const uint8_t* __restrict__ utype, float2* __restrict__ pos0,
+                            float2* __restrict__ vel0, float* __restrict__ rad,
+                            uint8_t* __restrict__ typ, int32_t* __restrict__ orig,
+                            uint32_t* __restrict__ count, int ncells, int* __restrict__ err) {
+    int stride = gridDim.x * blockDim.x;
+    int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int c = i0; c < ncells; c += stride) count[c] = 0u;
+    bool bad = false;
+    for (int i = i0; i < n; i += stride) {
+        float2 p = upos[i], v = uvel[i];
+        bad |= !(isfinite(p.x) && isfinite(p.y) && isfinite(v.x) && isfinite(v.y));
+        pos0[i] = p;
+        vel0[i] = v;
+        rad[i] = uradius[i];
+        typ[i] = utype[i];
+        orig[i] = i;
+    }
+    if (bad) atomicOr(err, ERR_BIT_NONFINITE);
+}
+
+// ------------------------------------------------------------- bin count ----
+template <class SRC>
+__global__ void bin_count_kernel(int n, SRC src, const float2* __restrict__ pos,
+                                 uint32_t* __restrict__ key, uint32_t* __restrict__ slot,
+                                 uint32_t* __restrict__ count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const SceneDev sc = src.get(i);
+    float2 p = pos[i];
+    int cx = cell_axis(p.x, sc.origin_x, sc.inv_cell, sc.nx);
+    int cy = cell_axis(p.y, sc.origin_y, sc.inv_cell, sc.ny);
+    uint32_t c = (uint32_t)(sc.cell_off + cy * sc.nx + cx);
+    key[i] = c;
+    slot[i] = atomicAdd(count + c, 1u);
+}
+
+// ------------------------------------------------------------------ scan ----
+// Exclusive scan of the cell counts into cell starts, three phases: per-block
+// scan of kScanChunk cells (writing block totals), scan of the block totals
+// (one block), and adding the block offsets.  Phase 1 also zeroes the counts
+// for the next step.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_sums,
+                                                    uint32_t& total) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = lane < nw ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    uint32_t pre = wid ? warp_sums[wid - 1] : 0u;
+    total = warp_sums[nw - 1];
+    __syncthreads();
+    return pre + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_blocks_kernel(uint32_t* __restrict__ count, uint32_t* __restrict__ start,
+                   uint32_t* __restrict__ bsum, int ncells) {
+    __shared__ uint32_t ws[32];
+    int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        int c = base + j;
+        v[j] = c < ncells ? count[c] : 0u;
+        s += v[j];
+    }
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        int c = base + j;
+        if (c < ncells) count[c] = 0u;
+    }
+    uint32_t total;
+    uint32_t pre = block_excl_scan(s, ws, total);
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        int c = base + j;
+        if (c < ncells) start[c] = pre;
+        pre += v[j];
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) scan_bsum_kernel(uint32_t* __restrict__ bsum, int nb) {
+    __shared__ uint32_t ws[32];
+    constexpr int kItems = 16;   // 1024 * 16 block totals = 2^26 cells
+    int base = threadIdx.x * kItems;
+    uint32_t v[kItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        v[j] = base + j < nb ? bsum[base + j] : 0u;
+        s += v[j];
+    }
+    uint32_t total;
+    uint32_t pre = block_excl_scan(s, ws, total);
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        if (base + j < nb) bsum[base + j] = pre;
+        pre += v[j];
+    }
+    if (threadIdx.x == 0) bsum[nb] = total;
+}
+
+__global__ void scan_add_kernel(uint32_t* __restrict__ start, const uint32_t* __restrict__ bsum,
+                                int ncells, int nb) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncells) start[c] += bsum[c / kScanChunk];
+    if (c == 0) start[ncells] = bsum[nb];
+}
+
+// --------------------------------------------------------------- scatter ----
+__global__ void scatter_kernel(int n, const uint32_t* __restrict__ key,
+                               const uint32_t* __restrict__ slot,
+                               const uint32_t* __restrict__ start,
+                               const float2* __restrict__ pos0, const float2* __restrict__ vel0,
+                               const float* __restrict__ rad_a, const uint8_t* __restrict__ typ_a,
+                               const int32_t* __restrict__ orig_a, float2* __restrict__ pos1,
+                               float2* __restrict__ vel1, float* __restrict__ rad_b,
+                               uint8_t* __restrict__ typ_b, int32_t* __restrict__ orig_b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t s = start[key[i]] + slot[i];
+    pos1[s] = pos0[i];
+    vel1[s] = vel0[i];
+    rad_b[s] = rad_a[i];
+    typ_b[s] = typ_a[i];
+    orig_b[s] = orig_a[i];
+}
+
+// ---------------------------------------------------------------- unload ----
+__global__ void unload_kernel(int n, const int32_t* __restrict__ orig,
+                              const float2* __restrict__ pos0, const float2* __restrict__ vel0,
+                              float2* __restrict__ upos, float2* __restrict__ uvel) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int o = orig[s];
+    upos[o] = pos0[s];
+    uvel[o] = vel0[s];
+}
+
+// ----------------------------------------------------------------- solve ----
+// One thread per agent (sorted slot s).  Lines are kept in dynamic shared
+// memory, line i of thread t at [i * blockDim.x + t] (conflict-free float4).
+// COUNT = true adds work tallies (algorithmic FLOP accounting); the
+// increments are dead code in the COUNT = false instantiation.
+template <int KCAP, class SRC, bool COUNT>
+__global__ void __launch_bounds__(128)
+solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __restrict__ vel,
+             const float* __restrict__ rad, const uint8_t* __restrict__ typ,
+             const int32_t* __restrict__ orig, const uint32_t* __restrict__ cstart,
+             AgentIn ain, const float2* __restrict__ vpd, float2* __restrict__ out_pos,
+             float2* __restrict__ out_vel, DebugOut dbg,
+             unsigned long long* __restrict__ counters) {
+    extern __shared__ float4 smem_lines[];
+    const int stride = blockDim.x;
+    float4* L = smem_lines + threadIdx.x;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const SceneDev sc = src.get(s);
+    const float2 p = pos[s];
+    const float2 v = vel[s];
+    const float r = rad[s];
+    const int ta = typ[s];
+    const int o = orig[s];
+    const int cx = cell_axis(p.x, sc.origin_x, sc.inv_cell, sc.nx);
+    const int cy = cell_axis(p.y, sc.origin_y, sc.inv_cell, sc.ny);
+
+    // ---- k nearest by (d^2, index), exact ring search over the grid ----
+    // The list holds k entries sorted by descending key; entry 0 is the
+    // current k-th nearest (the admission threshold), placeholders are +inf.
+    float kd[KCAP];
+    int ko[KCAP], ks[KCAP];
+#pragma unroll
+    for (int i = 0; i < KCAP; ++i) {
+        kd[i] = CUDART_INF_F;
+        ko[i] = INT_MAX;
+        ks[i] = -1;
+    }
+    const int k = sc.k;
+    float thr_d = CUDART_INF_F;
+    int thr_o = INT_MAX;
+    int cnt = 0;
+    int n_cand = 0, work = 0;
+    const float R2 = sc.R2;
+    const uint32_t* __restrict__ cs = cstart + sc.cell_off;
+
+    if (k > 0) {
+        const int nx = sc.nx, ny = sc.ny;
+        const int mmax = max(max(cx, nx - 1 - cx), max(cy, ny - 1 - cy));
+        for (int m = 0; m <= mmax; ++m) {
+            // ring m = row cy-m, row cy+m (each one contiguous run of cells)
+            // and the two side cells of every row strictly between them
+            const int x0 = max(cx - m, 0), x1 = min(cx + m, nx - 1);
+            const int ylo = cy - m, yhi = cy + m;
+            const int ya = max(ylo + 1, 0), yb = min(yhi - 1, ny - 1);
+            const int nr = (m == 0) ? 1 : 2 + 2 * max(0, yb - ya + 1);
+            for (int rr = 0; rr < nr; ++rr) {
+                int c0, c1;
+                if (rr < 2) {
+                    const int y = rr ? yhi : ylo;
+                    if (y < 0 || y >= ny) continue;
+                    c0 = y * nx + x0;
+                    c1 = y * nx + x1;
+                } else {
+                    const int q = rr - 2;
+                    const int y = ya + (q >> 1);
+                    const int x = (q & 1) ? cx + m : cx - m;
+                    if (x < 0 || x >= nx) continue;
+                    c0 = c1 = y * nx + x;
+                }
+                const int jb = (int)__ldg(cs + c0), je = (int)__ldg(cs + c1 + 1);
+                n_cand += je - jb;
+                for (int j = jb; j < je; ++j) {
+                    const float2 q = pos[j];
+                    const float d2 = key_d2(p.x, p.y, q.x, q.y);
+                    if (d2 < R2 && d2 <= thr_d && j != s) {
+                        const int oj = __ldg(orig + j);
+                        if (d2 < thr_d || oj < thr_o) {
+                            // entry 0 (the current k-th key) leaves; the
+                            // candidate drops into place in the descending list
+                            bool placed = false;
+#pragma unroll
+                            for (int i = 0; i < KCAP; ++i) {
+                                if (i < k) {
+                                    const bool has_next = i + 1 < k;
+                                    const float nd = has_next ? kd[(i + 1) % KCAP] : -CUDART_INF_F;
+                                    const int no = has_next ? ko[(i + 1) % KCAP] : INT_MIN;
+                                    const int nj = has_next ? ks[(i + 1) % KCAP] : -1;
+                                    const bool shift = !placed && (nd > d2 || (nd == d2 && no > oj));
+                                    const bool put = !placed && !shift;
+                                    kd[i] = shift ? nd : (put ? d2 : kd[i]);
+                                    ko[i] = shift ? no : (put ? oj : ko[i]);
+                                    ks[i] = shift ? nj : (put ? j : ks[i]);
+                                    placed = placed || put;
+                                }
+                            }
+                            cnt = min(cnt + 1, k);
+                            thr_d = kd[0];
+                            thr_o = ko[0];
+                        }
+                    }
+                }
+            }
+            // every agent outside rings 0..m is farther than (m - delta) cells
+            const float D = ((float)m - sc.ring_delta) * sc.cell_size;
+            if (D > 0.0f) {
+                const float D2 = D * D * 0.99999f;
+                if (D2 >= R2) break;
+                if (cnt >= k && thr_d < D2) break;
+            }
+        }
+    }
+
+    // ---- preferred velocity toward the goal or the current waypoint ----
+    float2 g = ain.goal[o];
+    const float vmax = ain.max_speed[o];
+    if (ain.route != nullptr) {
+        const int rt = ain.route[o];
+        if (rt >= 0) {
+            int wi = ain.wp_idx[o];
+            const float2* W = ain.waypoints + (size_t)rt * ain.n_waypoints;
+            float2 w = W[wi];
+            float wdx = __fsub_rn(w.x, p.x), wdy = __fsub_rn(w.y, p.y);
+            float w2 = __fadd_rn(__fmul_rn(wdx, wdx), __fmul_rn(wdy, wdy));
+            if (wi < ain.n_waypoints - 1 && w2 <= __fmul_rn(r, r)) ++wi;
+            g = W[wi];
+            ain.wp_idx[o] = (uint8_t)wi;
+        }
+    }
+    float vpx = 0.0f, vpy = 0.0f;
+    {
+        float gx = g.x - p.x, gy = g.y - p.y;
+        float gl = sqrtf(gx * gx + gy * gy);
+        if (gl > 0.0f) {
+            float f = fminf(vmax / gl, sc.inv_dt);
+            vpx = gx * f;
+            vpy = gy * f;
+        }
+        if (vpd != nullptr) {
+            float2 dl = vpd[o];
+            vpx += dl.x;
+            vpy += dl.y;
+        }
+    }
+
+    // ---- one ORCA half-plane per neighbour (Sec. 3.1) ----
+    // The neighbour list leaves registers through the line slots (unrolled,
+    // constant indices); the line loop then runs rolled over shared memory.
+    // Constraint m is the m-th nearest: list entry k - 1 - m.
+#pragma unroll
+    for (int i = 0; i < KCAP; ++i) {
+        if (i < k && i >= k - cnt)
+            L[(k - 1 - i) * stride] = make_float4(kd[i], __int_as_float(ks[i]), 0.0f, 0.0f);
+    }
+    if (dbg.nbr != nullptr) {
+        int32_t* nb = dbg.nbr + (size_t)o * dbg.k_stride;
+        for (int m = cnt; m < dbg.k_stride; ++m) nb[m] = -1;
+#pragma unroll
+        for (int i = 0; i < KCAP; ++i)
+            if (i < k && i >= k - cnt) nb[k - 1 - i] = ko[i];
+    }
+    bool any_overlap = false;
+    for (int i = 0; i < cnt; ++i) {
+        const float4 e = L[i * stride];
+        const int j = __float_as_int(e.y);
+        const float2 pj = pos[j], vj = vel[j];
+        const float rj = rad[j];
+        const int tb = typ[j];
+        const float rs = __fadd_rn(r, rj);
+        const bool ov = e.x <= __fmul_rn(rs, rs);
+        any_overlap |= ov;
+        const float f = tb ? (ta ? sc.f11 : sc.f01) : (ta ? sc.f10 : sc.f00);
+        L[i * stride] = orca_line(p.x, p.y, v.x, v.y, r, pj.x, pj.y, vj.x, vj.y, rj, f,
+                                  sc.inv_tau, sc.inv_dt, ov);
+    }
+
+    // ---- velocity LP, least-penetration fallback ----
+    float vx, vy;
+    uint8_t flags = any_overlap ? 4 : 0;
+    float tstar = 0.0f;
+    const int fail = lp2_project(L, stride, cnt, vmax, vpx, vpy, 0.0f, vx, vy, work);
+    if (fail < cnt) {
+        flags |= 1;
+        float v3x, v3y;
+        const float t3 = lp3_min_penetration(L, stride, cnt, vmax, v3x, v3y, work);
+        tstar = t3;
+        // projection of v_pref onto the minimisers: lines relaxed by t*
+        const float tr = fmaxf(t3, 0.0f) + kTieSlack;
+        for (int i = 0; i < cnt; ++i) {
+            float4 li = L[i * stride];
+            li.x += tr * li.w;
+            li.y -= tr * li.z;
+            L[i * stride] = li;
+        }
+        float rx, ry;
+        if (lp2_project(L, stride, cnt, vmax, vpx, vpy, kTieTol, rx, ry, work) == cnt) {
+            vx = rx;
+            vy = ry;
+        } else {
+            vx = v3x;
+            vy = v3y;
+        }
+    }
+
+    // ---- integrate ----
+    out_vel[s] = make_float2(vx, vy);
+    out_pos[s] = make_float2(__fadd_rn(p.x, __fmul_rn(sc.dt, vx)),
+                             __fadd_rn(p.y, __fmul_rn(sc.dt, vy)));
+
+    if (COUNT) {
+        unsigned long long c[kNumCounters] = {(unsigned long long)n_cand,
+                                              (unsigned long long)cnt,
+                                              (unsigned long long)work,
+                                              (unsigned long long)(flags & 1), 1ull};
+#pragma unroll
+        for (int q = 0; q < kNumCounters; ++q) atomicAdd(counters + q, c[q]);
+    }
+    if (dbg.cell != nullptr) dbg.cell[o] = cy * sc.nx + cx;
+    if (dbg.cnt != nullptr) dbg.cnt[o] = cnt;
+    if (dbg.flags != nullptr) dbg.flags[o] = flags;
+    if (dbg.tstar != nullptr) dbg.tstar[o] = tstar;
+}
+
+}  // namespace orca

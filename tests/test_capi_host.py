@@ -1,0 +1,109 @@
+"""Host-side checks of the C ABI (no GPU needed, no compute calls).
+
+The library must load, export every function include/orca.h declares, and
+reject bad arguments on the host before touching the device.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2008_11578_gb300 import _lib, api, scenes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(orca_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported():
+    L = _lib.load()
+    names = _declared("orca.h")
+    assert "orca_step" in names and "orca_scene_create" in names
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in _lib.SIGNATURES, f"{n} has no ctypes signature"
+
+
+def test_version_and_status_strings():
+    assert api.orca_abi_version() == 1
+    assert api.orca_status_string(0) == "ok"
+    assert "non-finite" in api.orca_status_string(4)
+    assert api.orca_status_string(99) == "unknown status"
+
+
+def _params(**kw):
+    p = api.make_params(scenes.OrcaParams())
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def test_workspace_bytes_and_parameter_validation():
+    b1 = api.orca_workspace_bytes(_params(), 1000)
+    b2 = api.orca_workspace_bytes(_params(), 2000)
+    assert 0 < b1 < b2 and b1 % 256 == 0
+    assert api.orca_workspace_bytes(_params(), 0) > 0
+    L = _lib.load()
+    out = ctypes.c_size_t()
+    for bad, code in [(dict(dt=0.0), 1), (dict(neighbor_dist=-1.0), 1),
+                      (dict(time_horizon=float("nan")), 1), (dict(cell_size=0.0), 1),
+                      (dict(max_neighbors=-1), 1), (dict(max_neighbors=33), 5),
+                      (dict(grid_nx=0), 1), (dict(grid_nx=1 << 14, grid_ny=1 << 14), 5),
+                      (dict(block_size=48), 1), (dict(block_size=256), 1)]:
+        p = _params(**bad)
+        assert L.orca_workspace_bytes(ctypes.byref(p), 10, ctypes.byref(out)) == code, bad
+    p = _params()
+    assert L.orca_workspace_bytes(ctypes.byref(p), -1, ctypes.byref(out)) == 1
+    assert L.orca_workspace_bytes(None, 10, ctypes.byref(out)) == 1
+
+
+def test_create_rejects_bad_arguments_on_host():
+    L = _lib.load()
+    p = _params()
+    h = ctypes.c_void_p()
+    a = _lib.OrcaAgents()
+    a.n_agents = 10
+    # null agent arrays
+    assert L.orca_scene_create(ctypes.byref(p), ctypes.byref(a), ctypes.c_void_p(4096),
+                               1 << 20, ctypes.byref(h)) == 1
+    fake = 1 << 40      # never dereferenced: validation fails before any access
+    for f in ("pos", "vel", "goal", "radius", "max_speed", "type"):
+        setattr(a, f, fake)
+    need = api.orca_workspace_bytes(p, 10)
+    # misaligned / missing / small workspace
+    assert L.orca_scene_create(ctypes.byref(p), ctypes.byref(a), ctypes.c_void_p(fake + 8),
+                               need, ctypes.byref(h)) == 1
+    assert L.orca_scene_create(ctypes.byref(p), ctypes.byref(a), None, need,
+                               ctypes.byref(h)) == 1
+    assert L.orca_scene_create(ctypes.byref(p), ctypes.byref(a), ctypes.c_void_p(fake),
+                               need - 256, ctypes.byref(h)) == 1
+    # misaligned float2 array
+    a.pos = fake + 4
+    assert L.orca_scene_create(ctypes.byref(p), ctypes.byref(a), ctypes.c_void_p(fake),
+                               need, ctypes.byref(h)) == 1
+    a.pos = fake
+    # a route without waypoints
+    a.route = fake
+    assert L.orca_scene_create(ctypes.byref(p), ctypes.byref(a), ctypes.c_void_p(fake),
+                               need, ctypes.byref(h)) == 1
+    a.route = None
+    # bad parameters
+    q = _params(max_neighbors=40)
+    assert L.orca_scene_create(ctypes.byref(q), ctypes.byref(a), ctypes.c_void_p(fake),
+                               need, ctypes.byref(h)) == 5
+    assert L.orca_scene_create(ctypes.byref(p), ctypes.byref(a), ctypes.c_void_p(fake),
+                               need, None) == 1
+
+
+def test_null_handles():
+    L = _lib.load()
+    assert L.orca_step(None, 1, None, None) == 1
+    assert L.orca_step_launch_count(None, 1) == -1
+    assert L.orca_scene_sync_status(None) == 1
+    assert L.orca_scene_set_debug(None, None, None, None, None, None) == 1
+    L.orca_scene_destroy(None)

@@ -1,0 +1,174 @@
+"""CUDA path against the FP64 oracle, element by element (needs a GPU).
+
+Every case runs one synchronous step (or a per-step rollout) on the GPU
+through the C ABI and the same step in the oracle from the identical FP32
+state, then checks cells, neighbour lists and waypoint indices bit for bit
+and velocities/positions within the stated tolerances (parity_util).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_11578_gb300 import api, scenes
+from tests.parity_util import compare, gpu_step
+
+pytestmark = pytest.mark.gpu
+
+
+def _cells_oracle(scene, cell_size=None):
+    p = scene.params
+    c = p.cell_size if cell_size is None else cell_size
+    nx, ny = p.grid_dims(c)
+    return oracle.cells(scene.pos, p.origin, np.float32(1.0 / np.float32(c)), nx, ny)
+
+
+def test_open_square_one_step():
+    s = scenes.open_square()
+    g = gpu_step(s)
+    assert g["status"] == 0
+    assert np.array_equal(g["cell"], _cells_oracle(s))
+    st = compare(s, g)
+    assert st["infeasible_oracle"] > 100   # uniform spawn overlaps: fallback exercised
+
+
+def test_open_square_per_step_rollout():
+    """Per-step parity from identical states along a 40-step GPU rollout."""
+    s = scenes.open_square()
+    for t in range(40):
+        g = gpu_step(s)
+        compare(s, g)
+        s.pos, s.vel = g["pos"], g["vel"]
+
+
+def test_shared_space_small():
+    s = scenes.shared_space(n_ped=6400, n_veh=100, side=160.0)
+    for t in range(3):
+        g = gpu_step(s)
+        assert np.array_equal(g["cell"], _cells_oracle(s))
+        compare(s, g)
+        s.pos, s.vel = g["pos"], g["vel"]
+
+
+def test_clusters_dense_sampled():
+    """Density of the 1M-agent cluster workload (15,625 agents per cluster),
+    four clusters; oracle on a sample that includes every fallback agent."""
+    s = scenes.clusters(n=62500, side=500.0, n_clusters_axis=2)
+    g = gpu_step(s)
+    rng = np.random.default_rng(0)
+    inf = np.nonzero(g["flags"] & 1)[0]
+    sel = np.unique(np.concatenate([rng.choice(s.n, 6000, replace=False),
+                                    rng.choice(inf, min(4000, len(inf)), replace=False)]))
+    assert np.array_equal(g["cell"], _cells_oracle(s))
+    st = compare(s, g, sel=sel)
+    assert st["infeasible_oracle"] > 1000
+
+
+def test_clusters_full_size_sampled():
+    """The 1M-agent workload at full size, launch configuration of the
+    benchmark; the oracle computes 3,000 sampled agents one by one."""
+    s = scenes.clusters()
+    g = gpu_step(s)
+    rng = np.random.default_rng(1)
+    sel = np.sort(rng.choice(s.n, 3000, replace=False))
+    assert np.array_equal(g["cell"], _cells_oracle(s))
+    compare(s, g, sel=sel)
+
+
+def test_waypoints_rollout():
+    s = scenes.waypoint_square()
+    for t in range(6):
+        g = gpu_step(s)
+        compare(s, g)
+        s.pos, s.vel, s.wp_idx = g["pos"], g["vel"], g["wp_idx"]
+
+
+def test_vpref_delta():
+    s = scenes.open_square(400, 30.0, seed=3)
+    d = np.random.default_rng(2).normal(0, 0.3, (1, s.n, 2)).astype(np.float32)
+    g = gpu_step(s, vpref_delta=d)
+    compare(s, g, vpref_delta=d[0])
+
+
+def test_results_independent_of_cell_and_block_size():
+    """The neighbour search is exact, so the grid and launch shape change
+    nothing: outputs are bitwise identical."""
+    s = scenes.open_square(1500, 60.0, seed=4)
+    ref = gpu_step(s, n_steps=3)
+    for c, b in [(0.7, 0), (5.0, 64), (13.0, 32), (61.0, 96), (2.0, 128)]:
+        g = gpu_step(s, n_steps=3, cell_size=c, block_size=b)
+        assert np.array_equal(g["pos"], ref["pos"]) and np.array_equal(g["vel"], ref["vel"])
+        assert np.array_equal(g["nbr"], ref["nbr"])
+
+
+def test_multi_step_call_equals_single_steps_and_is_deterministic():
+    s = scenes.open_square(800, 40.0, seed=8)
+    a = gpu_step(s, n_steps=5)
+    b = gpu_step(s, n_steps=5)
+    assert np.array_equal(a["pos"], b["pos"]) and np.array_equal(a["vel"], b["vel"])
+    c = s.copy()
+    for _ in range(5):
+        g = gpu_step(c)
+        c.pos, c.vel = g["pos"], g["vel"]
+    assert np.array_equal(a["pos"], c.pos) and np.array_equal(a["vel"], c.vel)
+
+
+# ------------------------------------------------------------ edge cases ----
+
+def test_empty_scene():
+    s = scenes.open_square(0, 10.0)
+    g = gpu_step(s)
+    assert g["status"] == 0 and g["pos"].shape == (0, 2)
+
+
+def test_single_agent_moves_to_goal():
+    s = scenes.open_square(1, 10.0, seed=9)
+    g = gpu_step(s)
+    compare(s, g)
+
+
+def test_k_zero_and_k_32():
+    for k in (0, 1, 32):
+        s = scenes.open_square(700, 30.0, seed=10)
+        s.params.max_neighbors = k
+        g = gpu_step(s)
+        compare(s, g)
+
+
+def test_all_agents_in_one_cell_and_outside_box():
+    s = scenes.open_square(600, 30.0, seed=11)
+    g = gpu_step(s, cell_size=1000.0)
+    compare(s, g)
+    t = s.copy()
+    t.pos = (t.pos * np.float32(2.0) - np.float32(20.0)).astype(np.float32)   # spills out of the box
+    g = gpu_step(t)
+    assert np.array_equal(g["cell"], _cells_oracle(t))
+    compare(t, g)
+
+
+def test_coincident_and_exact_ties():
+    """Agents on an exact lattice (many equal keys, broken by index) and two
+    agents at the same point."""
+    xs = np.arange(12, dtype=np.float32)
+    P = np.stack(np.meshgrid(xs, xs), -1).reshape(-1, 2).astype(np.float32)
+    P = np.concatenate([P, P[:1]])          # one duplicate position
+    n = len(P)
+    s = scenes.Scene(P, np.zeros_like(P), P[::-1].copy(), np.full(n, 0.3, np.float32),
+                     np.full(n, 1.5, np.float32), (np.arange(n) % 7 == 0).astype(np.uint8),
+                     scenes.OrcaParams(extent=(12.0, 12.0), cell_size=1.0))
+    g = gpu_step(s)
+    compare(s, g)
+
+
+def test_nonfinite_input_reports_status():
+    s = scenes.open_square(50, 10.0, seed=12)
+    s.pos[7, 0] = np.nan
+    g = gpu_step(s)
+    assert g["status"] == 4
+
+
+def test_launch_count():
+    s = scenes.open_square(100, 10.0)
+    ds = api.DeviceScene(s)
+    assert ds.launch_count(3) == 2 + 6 * 3
+    assert ds.launch_count(0) == 0
+    ds.close()
