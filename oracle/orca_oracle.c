@@ -223,13 +223,18 @@ static int project_enum(const oline *L, int n, double t, double vmax,
         /* projection onto the line */
         double s = bi - (nix * vpx + niy * vpy);
         consider(&b, L, n, t, vmax, vpx, vpy, vpx + s * nix, vpy + s * niy, slack);
-        /* line meets the circle */
+        /* line meets the circle; a line tangent to it (up to rounding)
+           meets it only at the tangent point, which is the single minimiser
+           when one half-plane alone attains t* on the circle */
         double h2 = r2 - bi * bi;
         if (h2 >= 0.0) {
             double h = sqrt(h2);
             double cx = bi * nix, cy = bi * niy;
             consider(&b, L, n, t, vmax, vpx, vpy, cx + h * L[i].dx, cy + h * L[i].dy, slack);
             consider(&b, L, n, t, vmax, vpx, vpy, cx - h * L[i].dx, cy - h * L[i].dy, slack);
+        } else {
+            double sg = bi > 0.0 ? vmax : -vmax;
+            consider(&b, L, n, t, vmax, vpx, vpy, sg * nix, sg * niy, slack);
         }
         /* line meets another line */
         for (int j = i + 1; j < n; ++j) {
