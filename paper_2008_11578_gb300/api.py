@@ -99,6 +99,26 @@ def orca_scene_set_counters(handle, counters=None):
     check(_lib.load().orca_scene_set_counters(handle, _ptr(counters)), "orca_scene_set_counters")
 
 
+_cudart = None
+
+
+def event_elapsed_ms(begin, end) -> float:
+    """Milliseconds between two torch CUDA events recorded by liborca (torch's
+    own elapsed_time only accepts events it recorded itself)."""
+    global _cudart
+    if _cudart is None:
+        _cudart = ctypes.CDLL("libcudart.so.13")
+        _cudart.cudaEventElapsedTime.argtypes = [ctypes.POINTER(ctypes.c_float),
+                                                 ctypes.c_void_p, ctypes.c_void_p]
+        _cudart.cudaEventElapsedTime.restype = ctypes.c_int
+    ms = ctypes.c_float(0.0)
+    rc = _cudart.cudaEventElapsedTime(ctypes.byref(ms), ctypes.c_void_p(begin.cuda_event),
+                                      ctypes.c_void_p(end.cuda_event))
+    if rc != 0:
+        raise RuntimeError(f"cudaEventElapsedTime failed ({rc})")
+    return float(ms.value)
+
+
 def orca_step(handle, n_steps: int, vpref_delta=None, stream=None):
     check(_lib.load().orca_step(handle, int(n_steps), _ptr(vpref_delta),
                                 _stream_handle(stream)), "orca_step")

@@ -77,9 +77,4 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanChunk = kScanThreads * kScanItems;   // cells per scan block
 
-// Slack and tolerance of the relaxed tie-break projection after the
-// least-penetration LP (absolute, m/s).
-constexpr float kTieSlack = 0.0f;
-constexpr float kTieTol = 1e-3f;
-
 }  // namespace orca

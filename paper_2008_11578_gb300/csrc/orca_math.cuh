@@ -135,18 +135,15 @@ __device__ __forceinline__ float penetration(float4 L, float vx, float vy) {
 // lines and the speed disc finds it.
 // ---------------------------------------------------------------------------
 
-// 1D problem on line i.  tol > 0 accepts intervals that are empty by at most
-// tol (rounding in the relaxed tie-break problem) and takes their midpoint.
+// 1D problem on line i: the point of line i closest to v_pref that keeps
+// lines 0..i-1 and the disc.  Returns false when that set is empty.
 __device__ __forceinline__ bool lp1_project(const float4* __restrict__ L, int stride, int i,
-                                            float vmax, float vpx, float vpy, float tol,
-                                            float& ox, float& oy, int& work) {
+                                            float vmax, float vpx, float vpy, float& ox,
+                                            float& oy, int& work) {
     float4 li = L[i * stride];
     float dot = li.x * li.z + li.y * li.w;
     float disc = dot * dot + vmax * vmax - (li.x * li.x + li.y * li.y);
-    if (disc < 0.0f) {
-        if (disc < -tol * (1.0f + vmax * vmax)) return false;
-        disc = 0.0f;
-    }
+    if (disc < 0.0f) return false;
     float sq = sqrtf(disc);
     float tl = -dot - sq, tr = -dot + sq;
     for (int j = 0; j < i; ++j) {
@@ -155,18 +152,13 @@ __device__ __forceinline__ bool lp1_project(const float4* __restrict__ L, int st
         float den = li.z * lj.w - li.w * lj.z;                     // det(d_i, d_j)
         float num = lj.z * (li.y - lj.y) - lj.w * (li.x - lj.x);   // det(d_j, P_i - P_j)
         if (den == 0.0f) {
-            if (num < -tol) return false;
+            if (num < 0.0f) return false;
             continue;
         }
         float t = num / den;
         if (den > 0.0f) tr = fminf(tr, t);
         else tl = fmaxf(tl, t);
-        if (tl > tr + tol) return false;
-    }
-    if (tl > tr) {
-        float m = 0.5f * (tl + tr);
-        tl = m;
-        tr = m;
+        if (tl > tr) return false;
     }
     float t = li.z * (vpx - li.x) + li.w * (vpy - li.y);
     t = fminf(fmaxf(t, tl), tr);
@@ -179,8 +171,8 @@ __device__ __forceinline__ bool lp1_project(const float4* __restrict__ L, int st
 // success, else the index of the line whose 1D problem was empty (v keeps
 // the optimum of the lines before it).
 __device__ __forceinline__ int lp2_project(const float4* __restrict__ L, int stride, int n,
-                                           float vmax, float vpx, float vpy, float tol,
-                                           float& vx, float& vy, int& work) {
+                                           float vmax, float vpx, float vpy, float& vx,
+                                           float& vy, int& work) {
     float vp2 = vpx * vpx + vpy * vpy;
     if (vp2 > vmax * vmax) {
         float s = vmax / sqrtf(vp2);
@@ -194,7 +186,7 @@ __device__ __forceinline__ int lp2_project(const float4* __restrict__ L, int str
         float4 li = L[i * stride];
         if (penetration(li, vx, vy) > 0.0f) {
             float ox, oy;
-            if (!lp1_project(L, stride, i, vmax, vpx, vpy, tol, ox, oy, work)) return i;
+            if (!lp1_project(L, stride, i, vmax, vpx, vpy, ox, oy, work)) return i;
             vx = ox;
             vy = oy;
         }
@@ -203,23 +195,22 @@ __device__ __forceinline__ int lp2_project(const float4* __restrict__ L, int str
 }
 
 // Boundary of {v : det_j(v) <= det_i(v)} as a line with its admissible side
-// on the left: direction (d_j - d_i) normalised, through the intersection of
-// lines i and j; for opposite parallel lines the mid-line.  Returns false for
-// same-direction parallel lines (one of them dominates everywhere).
+// on the left.  With n = (-d_y, d_x) and c = det(d, P) = n . P the set is
+// (n_j - n_i) . v >= c_j - c_i: normal a = n_j - n_i, offset b = c_j - c_i,
+// direction (a_y, -a_x)/|a|, anchored at its closest point to the origin
+// a b / |a|^2 (an intersection point would run off to infinity for nearly
+// opposite lines and lose all FP32 precision).  Returns false for parallel
+// lines of the same direction (one of them dominates everywhere).
 __device__ __forceinline__ bool bisector(float4 li, float4 lj, float4& b) {
-    float det = li.z * lj.w - li.w * lj.z;
-    float ex = lj.z - li.z, ey = lj.w - li.w;
-    float el2 = ex * ex + ey * ey;
-    if (fabsf(det) <= 1e-6f) {
-        if (li.z * lj.z + li.w * lj.w > 0.0f) return false;
-        float inv = rsqrtf(el2);
-        b = make_float4(0.5f * (li.x + lj.x), 0.5f * (li.y + lj.y), ex * inv, ey * inv);
-        return true;
-    }
-    // X = P_i + s d_i with s = det(d_j, P_j - P_i) / det(d_j, d_i)
-    float s = (lj.z * (lj.y - li.y) - lj.w * (lj.x - li.x)) / (-det);
-    float inv = rsqrtf(el2);
-    b = make_float4(li.x + s * li.z, li.y + s * li.w, ex * inv, ey * inv);
+    const float ax = li.w - lj.w;          // n_j - n_i, n = (-d_y, d_x)
+    const float ay = lj.z - li.z;
+    const float a2 = ax * ax + ay * ay;
+    if (a2 <= 1e-12f) return false;
+    const float ci = li.z * li.y - li.w * li.x;
+    const float cj = lj.z * lj.y - lj.w * lj.x;
+    const float s = (cj - ci) / a2;
+    const float inv = rsqrtf(a2);
+    b = make_float4(ax * s, ay * s, ay * inv, -ax * inv);
     return true;
 }
 
@@ -278,6 +269,84 @@ __device__ __forceinline__ float lp3_min_penetration(const float4* __restrict__ 
     float tm = -CUDART_INF_F;
     for (int i = 0; i < n; ++i) tm = fmaxf(tm, penetration(L[i * stride], vx, vy));
     return tm;
+}
+
+// The set of least-penetration velocities is one point unless two of the
+// half-planes attaining t* are exactly opposite (a valley between two
+// neighbours); then it is the part of the valley's mid-line that keeps every
+// other half-plane within t* and the disc, and the result is its point
+// closest to v_pref.  Returns true and writes that point for a valley.
+__device__ __forceinline__ bool valley_tie_break(const float4* __restrict__ L, int stride,
+                                                 int n, float t3, float vmax, float vpx,
+                                                 float vpy, float v3x, float v3y, float& ox,
+                                                 float& oy, int& work) {
+    const float atol = 1e-5f * (1.0f + fabsf(t3));
+    int vi = -1, vj = -1;
+    for (int i = 0; i < n && vi < 0; ++i) {
+        const float4 li = L[i * stride];
+        if (penetration(li, v3x, v3y) < t3 - atol) continue;
+        for (int j = i + 1; j < n; ++j) {
+            ++work;
+            const float4 lj = L[j * stride];
+            if (fabsf(li.z * lj.w - li.w * lj.z) > 2e-7f || li.z * lj.z + li.w * lj.w >= 0.0f)
+                continue;
+            if (penetration(lj, v3x, v3y) < t3 - atol) continue;
+            vi = i;
+            vj = j;
+            break;
+        }
+    }
+    if (vi < 0) return false;
+    float4 m;
+    if (!bisector(L[vi * stride], L[vj * stride], m)) return false;
+    const float dot = m.x * m.z + m.y * m.w;
+    const float disc = dot * dot + vmax * vmax - (m.x * m.x + m.y * m.y);
+    if (disc < 0.0f) return false;
+    const float sq = sqrtf(disc);
+    float tl = -dot - sq, tr = -dot + sq;
+    const float T = t3 + 1e-6f * (1.0f + fabsf(t3));
+    for (int k = 0; k < n; ++k) {
+        if (k == vi || k == vj) continue;
+        ++work;
+        const float4 lk = L[k * stride];
+        // det(d_k, P_k - (M + s e)) <= T  <=>  s det(e, d_k) <= T - det(d_k, P_k - M)
+        const float den = m.z * lk.w - m.w * lk.z;
+        const float num = T - (lk.z * (lk.y - m.y) - lk.w * (lk.x - m.x));
+        if (den == 0.0f) {
+            if (num < 0.0f) return false;
+            continue;
+        }
+        const float s = num / den;
+        if (den > 0.0f) tr = fminf(tr, s);
+        else tl = fmaxf(tl, s);
+    }
+    if (tl > tr) return false;
+    float s = m.z * (vpx - m.x) + m.w * (vpy - m.y);
+    s = fminf(fmaxf(s, tl), tr);
+    ox = m.x + s * m.z;
+    oy = m.y + s * m.w;
+    return true;
+}
+
+// The velocity of one agent (paper Sec. 3): the admissible velocity closest
+// to v_pref, else the velocity of least penetration.  Lines are consumed in
+// the order given.  Returns 1 when the half-planes were infeasible.
+__device__ __forceinline__ int solve_velocity(const float4* __restrict__ L, int stride, int n,
+                                              float vmax, float vpx, float vpy, float& vx,
+                                              float& vy, float& tstar, int& work) {
+    tstar = 0.0f;
+    if (lp2_project(L, stride, n, vmax, vpx, vpy, vx, vy, work) == n) return 0;
+    float v3x, v3y;
+    const float t3 = lp3_min_penetration(L, stride, n, vmax, v3x, v3y, work);
+    tstar = t3;
+    vx = v3x;
+    vy = v3y;
+    float ox, oy;
+    if (valley_tie_break(L, stride, n, t3, vmax, vpx, vpy, v3x, v3y, ox, oy, work)) {
+        vx = ox;
+        vy = oy;
+    }
+    return 1;
 }
 
 }  // namespace orca

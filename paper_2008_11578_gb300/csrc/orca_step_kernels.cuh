@@ -347,32 +347,9 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     }
 
     // ---- velocity LP, least-penetration fallback ----
-    float vx, vy;
-    uint8_t flags = any_overlap ? 4 : 0;
-    float tstar = 0.0f;
-    const int fail = lp2_project(L, stride, cnt, vmax, vpx, vpy, 0.0f, vx, vy, work);
-    if (fail < cnt) {
-        flags |= 1;
-        float v3x, v3y;
-        const float t3 = lp3_min_penetration(L, stride, cnt, vmax, v3x, v3y, work);
-        tstar = t3;
-        // projection of v_pref onto the minimisers: lines relaxed by t*
-        const float tr = fmaxf(t3, 0.0f) + kTieSlack;
-        for (int i = 0; i < cnt; ++i) {
-            float4 li = L[i * stride];
-            li.x += tr * li.w;
-            li.y -= tr * li.z;
-            L[i * stride] = li;
-        }
-        float rx, ry;
-        if (lp2_project(L, stride, cnt, vmax, vpx, vpy, kTieTol, rx, ry, work) == cnt) {
-            vx = rx;
-            vy = ry;
-        } else {
-            vx = v3x;
-            vy = v3y;
-        }
-    }
+    float vx, vy, tstar;
+    const int infeasible = solve_velocity(L, stride, cnt, vmax, vpx, vpy, vx, vy, tstar, work);
+    const uint8_t flags = (uint8_t)(infeasible | (any_overlap ? 4 : 0));
 
     // ---- integrate ----
     out_vel[s] = make_float2(vx, vy);
