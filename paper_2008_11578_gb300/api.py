@@ -89,6 +89,9 @@ def orca_scene_set_debug(handle, cell=None, nbr=None, cnt=None, flags=None, tsta
 def orca_scene_set_solve_events(handle, begin=None, end=None):
     """Bracket the solve kernel of every following step with two
     ``torch.cuda.Event(enable_timing=True)`` (or None to stop)."""
+    for ev in (begin, end):
+        if ev is not None and ev.cuda_event == 0:
+            ev.record()     # torch creates the CUDA event at its first record
     b = None if begin is None else ctypes.c_void_p(begin.cuda_event)
     e = None if end is None else ctypes.c_void_p(end.cuda_event)
     check(_lib.load().orca_scene_set_solve_events(handle, b, e), "orca_scene_set_solve_events")

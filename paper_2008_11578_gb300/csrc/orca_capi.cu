@@ -136,10 +136,17 @@ void launch_solve(int kcap, bool count, int grid, int block, size_t smem, cudaSt
                   const uint8_t* typ, const int32_t* orig, const uint32_t* start, AgentIn ain,
                   const float2* vpd, float2* out_pos, float2* out_vel, DebugOut dbg,
                   unsigned long long* counters) {
+    // more than 48 KB of dynamic shared memory needs an explicit opt-in
 #define ORCA_SOLVE(K, C)                                                                  \
-    solve_kernel<K, SRC, C><<<grid, block, smem, st>>>(n, src, pos, vel, rad, typ, orig, \
-                                                        start, ain, vpd, out_pos, out_vel, \
-                                                        dbg, counters)
+    do {                                                                                  \
+        if (smem > 48 * 1024)                                                             \
+            cudaFuncSetAttribute(solve_kernel<K, SRC, C>,                                 \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        solve_kernel<K, SRC, C><<<grid, block, smem, st>>>(n, src, pos, vel, rad, typ,    \
+                                                            orig, start, ain, vpd,        \
+                                                            out_pos, out_vel, dbg,        \
+                                                            counters);                    \
+    } while (0)
     if (kcap == 16) {
         if (count) ORCA_SOLVE(16, true);
         else ORCA_SOLVE(16, false);
