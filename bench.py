@@ -47,6 +47,35 @@ FLOPS_CAND, FLOPS_LINE, FLOPS_PAIR, FLOPS_AGENT = 5, 50, 10, 30
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
+def _source_hash():
+    import hashlib
+    root = os.path.join(ROOT, "paper_2008_11578_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(root)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(root, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "orca.h"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(workload):
+    """DRAM bytes per solve launch from the committed ncu summary, or None
+    when the CUDA sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", f"solve_kernel_{workload.split('_', 1)[0]}_1m.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    vals = dict(line.split(": ", 1) for line in txt.splitlines()
+                if line.startswith(("kernel_source_hash: ", "traffic_bytes_per_launch: ")))
+    if vals.get("kernel_source_hash", "").strip() != _source_hash():
+        return None
+    try:
+        return int(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -274,7 +303,8 @@ def run_ours(args):
     peak_tflops = 2 * FP32_LANES * SMS * SM_MAX_MHZ * 1e6 / 1e12
     achieved = flops / solve_avg_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
+                "frac": achieved / peak_tflops,
+                "traffic": _profiled_traffic(args.workload) if args.workload == "clusters_1m" else None,
                 "kernel": "solve_kernel", "solve_ms": statistics.mean(solve_ms),
                 "solve_share_of_step": statistics.mean(solve_ms) / statistics.mean(step_ms),
                 "flops_per_agent_step": flops / n,
