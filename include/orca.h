@@ -198,6 +198,40 @@ int orca_scene_sync_status(orca_scene *scene);
 /* Free the host object (the caller's device memory is untouched). */
 void orca_scene_destroy(orca_scene *scene);
 
+/*
+ * Bytes of the library's built-in scratch area used by orca_step_noalloc()
+ * (2 MiB, held in device memory by every GPU that loads the library, until
+ * the process exits).
+ */
+#define ORCA_NOALLOC_SCRATCH_BYTES (2u << 20)
+
+/*
+ * orca_step for callers that cannot allocate device memory themselves: code
+ * running inside another framework's memory pool, a plugin that may not
+ * call cudaMalloc, or a real-time loop that must never allocate.  The paper
+ * has no counterpart; it is a convenience of this library.
+ *
+ * Same inputs, outputs and step as creating a scene and calling orca_step,
+ * but no scene object and no caller workspace: the scratch lives in a fixed
+ * area inside the library.  This call performs no cudaMalloc, cudaFree or
+ * any other allocation.
+ *   - Size limit: the call is refused with ORCA_ERR_CAPACITY when
+ *     orca_workspace_bytes(params, agents->n_agents) exceeds
+ *     ORCA_NOALLOC_SCRATCH_BYTES (about 16,000 agents on a 256 x 256 grid).
+ *   - The first call on a device looks up the scratch area's device address
+ *     (once per device, with that device current).  Make that first call
+ *     before any stream capture.
+ *   - Every call, from every thread and stream, shares the one scratch area
+ *     and it keeps the last call's contents; the call clears what has to
+ *     start at zero.  Calls that overlap on the GPU race with each other:
+ *     serialise them (one stream, or events between streams).
+ *   - synchronize != 0 waits for the stream and also reports errors found
+ *     on the device (ORCA_ERR_NONFINITE); with 0 the call is asynchronous
+ *     and only host-side errors are returned.
+ */
+int orca_step_noalloc(const orca_params *params, const orca_agents *agents, int n_steps,
+                      const float *vpref_delta, void *stream, int synchronize);
+
 #ifdef __cplusplus
 }
 #endif

@@ -97,7 +97,10 @@ SIGNATURES = {
     "orca_step_launch_count": (_I, [_V, _I]),
     "orca_scene_sync_status": (_I, [_V]),
     "orca_scene_destroy": (None, [_V]),
+    "orca_step_noalloc": (_I, [ctypes.POINTER(OrcaParams), ctypes.POINTER(OrcaAgents), _I, _V,
+                               _V, _I]),
 }
+NOALLOC_SCRATCH_BYTES = 2 << 20
 
 STATUS = {0: "ORCA_OK", 1: "ORCA_ERR_INVALID_ARG", 2: "ORCA_ERR_CUDA",
           3: "ORCA_ERR_TIMEOUT", 4: "ORCA_ERR_NONFINITE", 5: "ORCA_ERR_CAPACITY"}

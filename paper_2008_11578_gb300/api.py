@@ -139,6 +139,18 @@ def orca_scene_destroy(handle) -> None:
     _lib.load().orca_scene_destroy(handle)
 
 
+def orca_step_noalloc(params: OrcaParams, agents: OrcaAgents, n_steps: int,
+                      vpref_delta=None, stream=None, synchronize: bool = False) -> int:
+    """orca_step without a scene or workspace, for callers that cannot
+    allocate device memory; scratch comes from a fixed 2 MiB area inside the
+    library, shared by all calls (serialise calls that could overlap on the
+    GPU).  Returns the C status (0 = ok) instead of raising, so callers can
+    tell a too-large scene (ORCA_ERR_CAPACITY) from other errors."""
+    return int(_lib.load().orca_step_noalloc(ctypes.byref(params), ctypes.byref(agents),
+                                             int(n_steps), _ptr(vpref_delta),
+                                             _stream_handle(stream), int(bool(synchronize))))
+
+
 # ------------------------------------------------------------- scene --------
 
 class DeviceScene:

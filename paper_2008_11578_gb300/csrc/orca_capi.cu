@@ -339,3 +339,119 @@ int orca_scene_sync_status(orca_scene* s) {
 void orca_scene_destroy(orca_scene* s) { delete s; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free step (orca_step_noalloc): the workspace is a fixed scratch
+// array compiled into the library instead of caller memory.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+// The scratch area.  In host code this name is only a stand-in for the
+// device symbol; its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[ORCA_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+char* g_noalloc_base[kNoallocMaxDevices] = {};
+
+// Device address of the scratch area on the current device, looked up once
+// per device.  Returns nullptr on failure.
+char* noalloc_base(int dev) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_base[dev] == nullptr) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr)
+            return nullptr;
+        g_noalloc_base[dev] = (char*)p;
+    }
+    return g_noalloc_base[dev];
+}
+
+}  // namespace
+
+extern "C" int orca_step_noalloc(const orca_params* params, const orca_agents* agents,
+                                 int n_steps, const float* vpref_delta, void* stream,
+                                 int synchronize) {
+    int st = check_params(params);
+    if (st != ORCA_OK) return st;
+    st = check_agents(agents);
+    if (st != ORCA_OK) return st;
+    if (n_steps < 0) return ORCA_ERR_INVALID_ARG;
+    if (vpref_delta && !aligned(vpref_delta, 8)) return ORCA_ERR_INVALID_ARG;
+    const size_t ncells = (size_t)params->grid_nx * (size_t)params->grid_ny;
+    const Layout L = make_layout((size_t)agents->n_agents, ncells);
+    if (L.total > (size_t)ORCA_NOALLOC_SCRATCH_BYTES) return ORCA_ERR_CAPACITY;
+    const int n = agents->n_agents;
+    if (n == 0 || n_steps == 0) return ORCA_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ORCA_ERR_CUDA;
+    if (dev < 0 || dev >= kNoallocMaxDevices) return ORCA_ERR_CAPACITY;
+    char* w = noalloc_base(dev);
+    if (w == nullptr) return ORCA_ERR_CUDA;
+    cudaStream_t stm = (cudaStream_t)stream;
+
+    int* err = (int*)(w + L.err);
+    uint32_t* count = (uint32_t*)(w + L.count);
+    uint32_t* start = (uint32_t*)(w + L.start);
+    uint32_t* bsum = (uint32_t*)(w + L.bsum);
+    uint32_t* key = (uint32_t*)(w + L.key);
+    uint32_t* slot = (uint32_t*)(w + L.slot);
+    float2* pos0 = (float2*)(w + L.pos0);
+    float2* vel0 = (float2*)(w + L.vel0);
+    float2* pos1 = (float2*)(w + L.pos1);
+    float2* vel1 = (float2*)(w + L.vel1);
+    float* rad[2] = {(float*)(w + L.rad[0]), (float*)(w + L.rad[1])};
+    uint8_t* typ[2] = {(uint8_t*)(w + L.typ[0]), (uint8_t*)(w + L.typ[1])};
+    int32_t* orig[2] = {(int32_t*)(w + L.orig[0]), (int32_t*)(w + L.orig[1])};
+
+    // the error word and the cell counts must start at zero; the load
+    // kernel clears the counts, the error word is cleared here
+    if (cudaMemsetAsync(err, 0, 16, stm) != cudaSuccess) return ORCA_ERR_CUDA;
+    const int ncell = (int)ncells;
+    const int nblocks = (int)((ncells + kScanChunk - 1) / kScanChunk);
+    const orca_agents& A = *agents;
+    const int tb = 256;
+    const int gb = (n + tb - 1) / tb;
+    {
+        int g = (std::max(n, ncell) + tb - 1) / tb;
+        g = std::min(g, 152 * 16);
+        load_kernel<<<g, tb, 0, stm>>>(n, (const float2*)A.pos, (const float2*)A.vel, A.radius,
+                                       A.type, pos0, vel0, rad[0], typ[0], orig[0], count, ncell,
+                                       err);
+    }
+    AgentIn ain{(const float2*)A.goal, A.max_speed, A.route, (const float2*)A.waypoints,
+                A.n_waypoints, A.wp_idx};
+    OneScene src{scene_dev(params, 0, n, 0)};
+    const DebugOut dbg{nullptr, nullptr, nullptr, nullptr, nullptr, params->max_neighbors};
+    const int kcap = params->max_neighbors <= 16 ? 16 : 32;
+    const int sb = params->block_size ? params->block_size : 128;
+    const int sgrid = (n + sb - 1) / sb;
+    const size_t smem = (size_t)kcap * sb * sizeof(float4);
+    int cur = 0;
+    for (int t = 0; t < n_steps; ++t) {
+        bin_count_kernel<OneScene><<<gb, tb, 0, stm>>>(n, src, pos0, key, slot, count);
+        scan_blocks_kernel<<<nblocks, kScanThreads, 0, stm>>>(count, start, bsum, ncell);
+        scan_bsum_kernel<<<1, 1024, 0, stm>>>(bsum, nblocks);
+        scan_add_kernel<<<(ncell + 255) / 256, 256, 0, stm>>>(start, bsum, ncell, nblocks);
+        scatter_kernel<<<gb, tb, 0, stm>>>(n, key, slot, start, pos0, vel0, rad[cur], typ[cur],
+                                           orig[cur], pos1, vel1, rad[1 - cur], typ[1 - cur],
+                                           orig[1 - cur]);
+        cur = 1 - cur;
+        const float2* vpd =
+            vpref_delta ? (const float2*)vpref_delta + (size_t)t * (size_t)n : nullptr;
+        launch_solve(kcap, false, sgrid, sb, smem, stm, n, src, pos1, vel1, rad[cur], typ[cur],
+                     orig[cur], start, ain, vpd, pos0, vel0, dbg, nullptr);
+    }
+    unload_kernel<<<gb, tb, 0, stm>>>(n, orig[cur], pos0, vel0, (float2*)A.pos, (float2*)A.vel);
+    if (cudaGetLastError() != cudaSuccess) return ORCA_ERR_CUDA;
+    if (synchronize) {
+        if (cudaStreamSynchronize(stm) != cudaSuccess) return ORCA_ERR_CUDA;
+        int h[4] = {0, 0, 0, 0};
+        if (cudaMemcpy(h, err, 16, cudaMemcpyDeviceToHost) != cudaSuccess) return ORCA_ERR_CUDA;
+        if (h[0] & ERR_BIT_NONFINITE) return ORCA_ERR_NONFINITE;
+        if (h[0] & ERR_BIT_TIMEOUT) return ORCA_ERR_TIMEOUT;
+    }
+    return ORCA_OK;
+}
