@@ -233,6 +233,73 @@ def cpu_baseline(scene, cfg, budget_s=12.0):
                       f"({dt:.1f} s, FP64, brute-force neighbours)"}
 
 
+def measure_batched(dev, flush, n_steps=50, tune=True):
+    """512 independent scenes (log-uniform sizes in [100, 20,000]): one CUDA
+    graph of ``n_steps`` batched steps against the plain loop that calls
+    orca_step(n_steps) scene by scene.  Both start from the same state and
+    must end bit-identical."""
+    import torch
+
+    from paper_2008_11578_gb300 import api, autotune, scenes
+    sl = scenes.batched()
+    total = sum(s.n for s in sl)
+    stream = torch.cuda.current_stream()
+    tuned = None
+    cells = None
+    block = 0
+    if tune:
+        tuned = autotune.tune_batch(sl, dev, steps=3, warmup=1)
+        cells = tuned.cell_sizes(sl)
+        block = tuned.block_size
+    b = api.DeviceBatch(sl, dev, cell_sizes=cells, block_size=block)
+    pos0, vel0 = b.pos.clone(), b.vel.clone()
+    b.capture(n_steps)
+    b.replay()                                   # warm-up replay
+    torch.cuda.synchronize()
+    b.pos.copy_(pos0)
+    b.vel.copy_(vel0)
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.replay(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1)
+    status = b.sync_status()
+
+    plain = [api.DeviceScene(s, dev, cell_size=None if cells is None else cells[i],
+                             block_size=block) for i, s in enumerate(sl)]
+    for ds in plain:                             # warm-up call per scene
+        ds.step(1)
+    torch.cuda.synchronize()
+    for ds, s in zip(plain, sl):
+        ds.set_state(pos=s.pos, vel=s.vel)
+    torch.cuda.synchronize()
+    flush.zero_()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for ds in plain:
+        ds.step(n_steps)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    loop_ms = p0.elapsed_time(p1)
+    same = all(torch.equal(ds.pos, b.pos[b.scene_slice(i)]) and
+               torch.equal(ds.vel, b.vel[b.scene_slice(i)]) for i, ds in enumerate(plain))
+    for ds in plain:
+        ds.close()
+    b.close()
+    return {"workload": "batched_512", "scenes": len(sl), "agents": total,
+            "steps": n_steps, "graph_value": total * n_steps / (graph_ms / 1e3),
+            "plain_loop_value": total * n_steps / (loop_ms / 1e3), "unit": METRIC,
+            "graph_ms": graph_ms, "plain_loop_ms": loop_ms,
+            "speedup_vs_plain_loop": loop_ms / graph_ms, "bitwise_equal": bool(same),
+            "graph_launches": 2 + 6 * n_steps, "plain_loop_launches": len(sl) * (2 + 6 * n_steps),
+            "status": status,
+            "autotune": None if tuned is None else
+            {"alpha": tuned.alpha, "block_size": tuned.block_size,
+             "candidates": [[a, bs, ms] for a, bs, ms in tuned.table]}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -355,6 +422,8 @@ def run_ours(args):
             "clocks": clocks, "gpu_launches": ds.launch_count(1) * args.steps,
             "roofline": roofline, "e2e": e2e, "status": status,
             "hbm_peak_gbs": peaks.get("hbm_gbs")}
+    if not args.no_batched:
+        line["batched"] = measure_batched(dev, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, cfg)
     if rank == 0:
@@ -374,6 +443,7 @@ def main():
     ap.add_argument("--cell-size", type=float, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -53,8 +53,10 @@ extern "C" {
 
 /* largest max_neighbors the kernels are compiled for */
 #define ORCA_MAX_NEIGHBORS 32
-/* largest number of grid cells of one scene */
+/* largest number of grid cells of one scene, and of all scenes of a batch */
 #define ORCA_MAX_CELLS (1 << 26)
+/* largest number of scenes in one batch */
+#define ORCA_MAX_SCENES (1 << 20)
 
 /* debug_flags bits */
 #define ORCA_DEBUG_NONE 0u
@@ -190,13 +192,81 @@ int orca_scene_set_counters(orca_scene *scene, unsigned long long *counters);
 int orca_step_launch_count(const orca_scene *scene, int n_steps);
 
 /*
+ * Record n_steps of orca_step (same arguments) into a CUDA graph kept by the
+ * scene, replacing an earlier one.  Capture runs on a private stream and
+ * executes nothing; orca_scene_graph_launch() then replays the recorded
+ * launches on any stream with one call.  The graph holds the pointers of
+ * this call (vpref_delta included), so each replay reads the same arrays.
+ * Timing events and work counters are not recorded into the graph.
+ */
+int orca_scene_graph_capture(orca_scene *scene, int n_steps, const float *vpref_delta);
+
+/* Replay the captured graph on `stream` (ORCA_ERR_INVALID_ARG if none). */
+int orca_scene_graph_launch(orca_scene *scene, void *stream);
+
+/*
  * Synchronise the device, then read and clear the scene's device error
  * word.  Returns ORCA_OK or the first recorded error status.
  */
 int orca_scene_sync_status(orca_scene *scene);
 
-/* Free the host object (the caller's device memory is untouched). */
+/* Free the host object and its graph (the caller's memory is untouched). */
 void orca_scene_destroy(orca_scene *scene);
+
+/*
+ * ---------------------------------------------------------------------------
+ * Batches: many independent scenes of uneven size advanced by one launch per
+ * phase of the step.  The paper simulates one scene at a time (Sec. 4);
+ * every scene of a batch computes exactly what orca_step computes for it
+ * alone, bit for bit.
+ *
+ * The agents of all scenes are concatenated, scene 0 first, into ONE
+ * orca_agents (n_agents = total).  offsets is a HOST int array of
+ * n_scenes + 1 entries: scene s owns agents [offsets[s], offsets[s + 1]),
+ * offsets[0] = 0 and offsets[n_scenes] = n_agents.  params is a HOST array
+ * of n_scenes orca_params (each scene has its own grid box, neighbour
+ * distance, k, tau, dt and f table); block_size and debug_flags must be the
+ * same in all of them.  route entries index rows of the one concatenated
+ * waypoints array.  Agents of different scenes never interact.
+ * ---------------------------------------------------------------------------
+ */
+
+/* Workspace bytes of a batch (the agent total is offsets[n_scenes]). */
+int orca_batch_workspace_bytes(const orca_params *params, int n_scenes, const int *offsets,
+                               size_t *out_bytes);
+
+/*
+ * Create a batch over caller-owned arrays and workspace.  Validates on the
+ * host, then copies the scene table (n_scenes * 80 bytes) and the scene id
+ * of every agent (4 bytes each) into the workspace with cudaMemcpy.
+ */
+int orca_batch_create(const orca_params *params, int n_scenes, const int *offsets,
+                      const orca_agents *agents, void *workspace, size_t workspace_bytes,
+                      orca_batch **out);
+
+/* Per-agent diagnostics as orca_scene_set_debug; nbr rows have max_k
+   entries (the largest k of the batch) and hold concatenated indices; cell
+   ids are local to each scene's grid. */
+int orca_batch_set_debug(orca_batch *batch, int32_t *cell, int32_t *nbr, int32_t *cnt,
+                         uint8_t *flags, float *tstar);
+
+/* Advance every scene n_steps steps; vpref_delta is NULL or
+   float2[n_steps * n_agents] in the concatenated order. */
+int orca_step_batched(orca_batch *batch, int n_steps, const float *vpref_delta, void *stream);
+
+/* Number of kernel launches one orca_step_batched call of n_steps makes
+   (independent of the number of scenes). */
+int orca_batch_launch_count(const orca_batch *batch, int n_steps);
+
+/* CUDA graph of n_steps batched steps, as orca_scene_graph_capture. */
+int orca_batch_graph_capture(orca_batch *batch, int n_steps, const float *vpref_delta);
+int orca_batch_graph_launch(orca_batch *batch, void *stream);
+
+/* Device error word of the batch, as orca_scene_sync_status. */
+int orca_batch_sync_status(orca_batch *batch);
+
+/* Free the host object and its graph. */
+void orca_batch_destroy(orca_batch *batch);
 
 /*
  * Bytes of the library's built-in scratch area used by orca_step_noalloc()

@@ -95,8 +95,23 @@ SIGNATURES = {
     "orca_scene_set_counters": (_I, [_V, _V]),
     "orca_step": (_I, [_V, _I, _V, _V]),
     "orca_step_launch_count": (_I, [_V, _I]),
+    "orca_scene_graph_capture": (_I, [_V, _I, _V]),
+    "orca_scene_graph_launch": (_I, [_V, _V]),
     "orca_scene_sync_status": (_I, [_V]),
     "orca_scene_destroy": (None, [_V]),
+    "orca_batch_workspace_bytes": (_I, [ctypes.POINTER(OrcaParams), _I,
+                                       ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_size_t)]),
+    "orca_batch_create": (_I, [ctypes.POINTER(OrcaParams), _I, ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(OrcaAgents), _V, ctypes.c_size_t,
+                               ctypes.POINTER(_V)]),
+    "orca_batch_set_debug": (_I, [_V, _V, _V, _V, _V, _V]),
+    "orca_step_batched": (_I, [_V, _I, _V, _V]),
+    "orca_batch_launch_count": (_I, [_V, _I]),
+    "orca_batch_graph_capture": (_I, [_V, _I, _V]),
+    "orca_batch_graph_launch": (_I, [_V, _V]),
+    "orca_batch_sync_status": (_I, [_V]),
+    "orca_batch_destroy": (None, [_V]),
     "orca_step_noalloc": (_I, [ctypes.POINTER(OrcaParams), ctypes.POINTER(OrcaAgents), _I, _V,
                                _V, _I]),
 }

@@ -127,6 +127,16 @@ def orca_step(handle, n_steps: int, vpref_delta=None, stream=None):
                                 _stream_handle(stream)), "orca_step")
 
 
+def orca_scene_graph_capture(handle, n_steps: int, vpref_delta=None):
+    check(_lib.load().orca_scene_graph_capture(handle, int(n_steps), _ptr(vpref_delta)),
+          "orca_scene_graph_capture")
+
+
+def orca_scene_graph_launch(handle, stream=None):
+    check(_lib.load().orca_scene_graph_launch(handle, _stream_handle(stream)),
+          "orca_scene_graph_launch")
+
+
 def orca_step_launch_count(handle, n_steps: int) -> int:
     return int(_lib.load().orca_step_launch_count(handle, int(n_steps)))
 
@@ -149,6 +159,66 @@ def orca_step_noalloc(params: OrcaParams, agents: OrcaAgents, n_steps: int,
     return int(_lib.load().orca_step_noalloc(ctypes.byref(params), ctypes.byref(agents),
                                              int(n_steps), _ptr(vpref_delta),
                                              _stream_handle(stream), int(bool(synchronize))))
+
+
+def _params_array(params_list):
+    arr = (OrcaParams * len(params_list))()
+    for i, p in enumerate(params_list):
+        arr[i] = p
+    return arr
+
+
+def _offsets_array(offsets):
+    return (ctypes.c_int * len(offsets))(*[int(o) for o in offsets])
+
+
+def orca_batch_workspace_bytes(params_list, offsets) -> int:
+    out = ctypes.c_size_t(0)
+    check(_lib.load().orca_batch_workspace_bytes(_params_array(params_list), len(params_list),
+                                                 _offsets_array(offsets), ctypes.byref(out)),
+          "orca_batch_workspace_bytes")
+    return int(out.value)
+
+
+def orca_batch_create(params_list, offsets, agents: OrcaAgents, workspace, ws_bytes: int):
+    h = ctypes.c_void_p()
+    check(_lib.load().orca_batch_create(_params_array(params_list), len(params_list),
+                                        _offsets_array(offsets), ctypes.byref(agents),
+                                        _ptr(workspace), int(ws_bytes), ctypes.byref(h)),
+          "orca_batch_create")
+    return h
+
+
+def orca_batch_set_debug(handle, cell=None, nbr=None, cnt=None, flags=None, tstar=None):
+    check(_lib.load().orca_batch_set_debug(handle, _ptr(cell), _ptr(nbr), _ptr(cnt),
+                                           _ptr(flags), _ptr(tstar)), "orca_batch_set_debug")
+
+
+def orca_step_batched(handle, n_steps: int, vpref_delta=None, stream=None):
+    check(_lib.load().orca_step_batched(handle, int(n_steps), _ptr(vpref_delta),
+                                        _stream_handle(stream)), "orca_step_batched")
+
+
+def orca_batch_launch_count(handle, n_steps: int) -> int:
+    return int(_lib.load().orca_batch_launch_count(handle, int(n_steps)))
+
+
+def orca_batch_graph_capture(handle, n_steps: int, vpref_delta=None):
+    check(_lib.load().orca_batch_graph_capture(handle, int(n_steps), _ptr(vpref_delta)),
+          "orca_batch_graph_capture")
+
+
+def orca_batch_graph_launch(handle, stream=None):
+    check(_lib.load().orca_batch_graph_launch(handle, _stream_handle(stream)),
+          "orca_batch_graph_launch")
+
+
+def orca_batch_sync_status(handle) -> int:
+    return int(_lib.load().orca_batch_sync_status(handle))
+
+
+def orca_batch_destroy(handle) -> None:
+    _lib.load().orca_batch_destroy(handle)
 
 
 # ------------------------------------------------------------- scene --------
@@ -227,6 +297,14 @@ class DeviceScene:
             assert vpref_delta.numel() == 2 * n_steps * self.n
         orca_step(self.handle, n_steps, vpref_delta, stream)
 
+    def capture(self, n_steps: int, vpref_delta=None):
+        """Record ``n_steps`` steps into the scene's CUDA graph."""
+        orca_scene_graph_capture(self.handle, n_steps, vpref_delta)
+
+    def replay(self, stream=None):
+        """Launch the recorded graph on ``stream`` (torch's current one)."""
+        orca_scene_graph_launch(self.handle, stream)
+
     def launch_count(self, n_steps: int) -> int:
         return orca_step_launch_count(self.handle, n_steps)
 
@@ -236,6 +314,126 @@ class DeviceScene:
     def close(self):
         if getattr(self, "handle", None):
             orca_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DeviceBatch:
+    """Many independent scenes advanced together by one launch per phase.
+
+    ``scene_list`` holds :class:`scenes.Scene` objects; their agents are
+    concatenated (scene 0 first) into the device tensors ``pos``, ``vel`` ...
+    and ``offsets[s]:offsets[s + 1]`` is scene ``s``'s slice.  Routes are
+    re-based onto the concatenated waypoint rows.  ``cell_sizes`` (one per
+    scene, or None for each scene's default) only changes speed, never
+    results.
+    """
+
+    def __init__(self, scene_list, device="cuda", cell_sizes=None, block_size=0, debug=False):
+        torch = _torch()
+        self.device = torch.device(device)
+        dev = self.device
+        self.scenes = list(scene_list)
+        S = len(self.scenes)
+        if S == 0:
+            raise ValueError("a batch needs at least one scene")
+        sizes = [sc.n for sc in self.scenes]
+        self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        self.n = int(self.offsets[-1])
+        if cell_sizes is None:
+            cell_sizes = [None] * S
+        self.params_list = [make_params(sc.params, c, block_size)
+                            for sc, c in zip(self.scenes, cell_sizes)]
+        self.kmax = max(int(p.max_neighbors) for p in self.params_list)
+
+        def cat(get, dtype):
+            return torch.as_tensor(np.ascontiguousarray(np.concatenate(
+                [get(sc) for sc in self.scenes])), device=dev, dtype=dtype)
+
+        self.pos = cat(lambda sc: sc.pos.reshape(-1, 2), torch.float32)
+        self.vel = cat(lambda sc: sc.vel.reshape(-1, 2), torch.float32)
+        self.goal = cat(lambda sc: sc.goal.reshape(-1, 2), torch.float32)
+        self.radius = cat(lambda sc: sc.radius, torch.float32)
+        self.max_speed = cat(lambda sc: sc.max_speed, torch.float32)
+        self.type = cat(lambda sc: sc.type, torch.uint8)
+        self.route = self.waypoints = self.wp_idx = None
+        routed = [sc for sc in self.scenes if sc.route is not None]
+        n_wp = 0
+        n_routes = 0
+        if routed:
+            n_wp = int(routed[0].waypoints.shape[1])
+            if any(int(sc.waypoints.shape[1]) != n_wp for sc in routed):
+                raise ValueError("all routed scenes of a batch need the same waypoint count")
+            rows, routes, row0 = [], [], 0
+            for sc in self.scenes:
+                if sc.route is None:
+                    routes.append(np.full(sc.n, -1, np.int32))
+                else:
+                    r = sc.route.astype(np.int64)
+                    routes.append(np.where(r >= 0, r + row0, -1).astype(np.int32))
+                    rows.append(sc.waypoints.reshape(-1, n_wp, 2))
+                    row0 += sc.waypoints.shape[0]
+            n_routes = row0
+            self.route = torch.as_tensor(np.concatenate(routes), device=dev, dtype=torch.int32)
+            self.waypoints = torch.as_tensor(np.ascontiguousarray(
+                np.concatenate(rows).reshape(-1, 2)), device=dev, dtype=torch.float32)
+            self.wp_idx = cat(lambda sc: sc.wp_idx if sc.wp_idx is not None
+                              else np.zeros(sc.n, np.uint8), torch.uint8)
+        self.ws_bytes = orca_batch_workspace_bytes(self.params_list, self.offsets)
+        self.workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
+        a = OrcaAgents()
+        a.n_agents = self.n
+        a.pos, a.vel, a.goal = _ptr(self.pos), _ptr(self.vel), _ptr(self.goal)
+        a.radius, a.max_speed, a.type = _ptr(self.radius), _ptr(self.max_speed), _ptr(self.type)
+        a.route = _ptr(self.route)
+        a.waypoints = _ptr(self.waypoints)
+        a.n_routes = n_routes
+        a.n_waypoints = n_wp
+        a.wp_idx = _ptr(self.wp_idx)
+        self._agents = a
+        self.handle = orca_batch_create(self.params_list, self.offsets, a, self.workspace,
+                                        self.ws_bytes)
+        self.dbg = None
+        if debug:
+            self.enable_debug()
+
+    def enable_debug(self):
+        torch = _torch()
+        n, k, dev = self.n, max(self.kmax, 1), self.device
+        self.dbg = dict(cell=torch.full((n,), -1, dtype=torch.int32, device=dev),
+                        nbr=torch.full((n, k), -1, dtype=torch.int32, device=dev),
+                        cnt=torch.zeros(n, dtype=torch.int32, device=dev),
+                        flags=torch.zeros(n, dtype=torch.uint8, device=dev),
+                        tstar=torch.zeros(n, dtype=torch.float32, device=dev))
+        orca_batch_set_debug(self.handle, **self.dbg)
+
+    def scene_slice(self, s: int) -> slice:
+        return slice(int(self.offsets[s]), int(self.offsets[s + 1]))
+
+    def step(self, n_steps: int = 1, vpref_delta=None, stream=None):
+        orca_step_batched(self.handle, n_steps, vpref_delta, stream)
+
+    def capture(self, n_steps: int, vpref_delta=None):
+        """Record ``n_steps`` batched steps into the batch's CUDA graph."""
+        orca_batch_graph_capture(self.handle, n_steps, vpref_delta)
+
+    def replay(self, stream=None):
+        orca_batch_graph_launch(self.handle, stream)
+
+    def launch_count(self, n_steps: int) -> int:
+        return orca_batch_launch_count(self.handle, n_steps)
+
+    def sync_status(self) -> int:
+        return orca_batch_sync_status(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            orca_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

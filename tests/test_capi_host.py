@@ -30,7 +30,7 @@ def test_every_declared_symbol_is_exported():
 
 
 def test_version_and_status_strings():
-    assert api.orca_abi_version() == 1
+    assert api.orca_abi_version() == 2
     assert api.orca_status_string(0) == "ok"
     assert "non-finite" in api.orca_status_string(4)
     assert api.orca_status_string(99) == "unknown status"
@@ -107,3 +107,52 @@ def test_null_handles():
     assert L.orca_scene_sync_status(None) == 1
     assert L.orca_scene_set_debug(None, None, None, None, None, None) == 1
     L.orca_scene_destroy(None)
+
+
+def test_batch_validation_on_host():
+    L = _lib.load()
+    plist = [_params(), _params(grid_nx=10, grid_ny=10), _params()]
+    out = ctypes.c_size_t()
+    off = api._offsets_array([0, 5, 5, 12])
+    arr = api._params_array(plist)
+    assert L.orca_batch_workspace_bytes(arr, 3, off, ctypes.byref(out)) == 0
+    one = ctypes.c_size_t()
+    assert L.orca_workspace_bytes(ctypes.byref(plist[0]), 12, ctypes.byref(one)) == 0
+    assert out.value > one.value and out.value % 256 == 0
+    # offsets must start at 0 and not decrease
+    assert L.orca_batch_workspace_bytes(arr, 3, api._offsets_array([1, 5, 5, 12]),
+                                        ctypes.byref(out)) == 1
+    assert L.orca_batch_workspace_bytes(arr, 3, api._offsets_array([0, 6, 5, 12]),
+                                        ctypes.byref(out)) == 1
+    assert L.orca_batch_workspace_bytes(arr, 0, off, ctypes.byref(out)) == 1
+    # every scene shares the launch shape
+    bad = api._params_array([_params(), _params(block_size=64), _params()])
+    assert L.orca_batch_workspace_bytes(bad, 3, off, ctypes.byref(out)) == 1
+    # per-scene parameter errors surface with their own code
+    bad = api._params_array([_params(), _params(max_neighbors=40), _params()])
+    assert L.orca_batch_workspace_bytes(bad, 3, off, ctypes.byref(out)) == 5
+    # the cell total of all scenes is bounded
+    big = api._params_array([_params(grid_nx=1 << 13, grid_ny=1 << 13)] * 3)
+    assert L.orca_batch_workspace_bytes(big, 3, off, ctypes.byref(out)) == 5
+    # create: offsets must end at n_agents
+    a = _lib.OrcaAgents()
+    a.n_agents = 13
+    fake = 1 << 40
+    for f in ("pos", "vel", "goal", "radius", "max_speed", "type"):
+        setattr(a, f, fake)
+    h = ctypes.c_void_p()
+    assert L.orca_batch_create(arr, 3, off, ctypes.byref(a), ctypes.c_void_p(fake), 1 << 30,
+                               ctypes.byref(h)) == 1
+    a.n_agents = 12
+    assert L.orca_batch_create(arr, 3, off, ctypes.byref(a), ctypes.c_void_p(fake + 16),
+                               1 << 30, ctypes.byref(h)) == 1
+    assert L.orca_batch_create(arr, 3, off, ctypes.byref(a), ctypes.c_void_p(fake), 256,
+                               ctypes.byref(h)) == 1
+    assert L.orca_step_batched(None, 1, None, None) == 1
+    assert L.orca_batch_launch_count(None, 1) == -1
+    assert L.orca_batch_graph_capture(None, 1, None) == 1
+    assert L.orca_batch_graph_launch(None, None) == 1
+    assert L.orca_scene_graph_capture(None, 1, None) == 1
+    assert L.orca_scene_graph_launch(None, None) == 1
+    assert L.orca_batch_sync_status(None) == 1
+    L.orca_batch_destroy(None)
