@@ -360,6 +360,29 @@ static double active_cond(const oline *L, int n, double t, double vmax,
 }
 
 /*
+ * Whether two half-planes that attain t* at the minimiser (ax, ay) point in
+ * exactly opposite directions.  Only then is the set of least-penetration
+ * velocities a segment (a valley between the two); otherwise the maximum of
+ * the penetrations grows in every direction and the minimiser is the point.
+ */
+static int valley_at(const oline *L, int n, double t, double vmax, double ax, double ay)
+{
+    double scale = 1.0 + vmax;
+    for (int i = 0; i < n; ++i) {
+        double ci = L[i].dx * L[i].py - L[i].dy * L[i].px;
+        if (fabs(pen(&L[i], ax, ay) - t) > 1e-9 * (scale + fabs(ci) + fabs(t))) continue;
+        for (int j = i + 1; j < n; ++j) {
+            double cj = L[j].dx * L[j].py - L[j].dy * L[j].px;
+            if (fabs(pen(&L[j], ax, ay) - t) > 1e-9 * (scale + fabs(cj) + fabs(t))) continue;
+            double dot = L[i].dx * L[j].dx + L[i].dy * L[j].dy;
+            double det = L[i].dx * L[j].dy - L[i].dy * L[j].dx;
+            if (dot < 0.0 && fabs(det) <= 1e-12) return 1;
+        }
+    }
+    return 0;
+}
+
+/*
  * The velocity LP of one agent.  Writes v*, t* and returns flags:
  *   bit0 = constraints infeasible (t* > 0, least-penetration result)
  *   bit1 = enumeration found no candidate even with widened tolerances
@@ -376,6 +399,13 @@ static int lp_solve(const oline *L, int n, double vmax, double vpx, double vpy,
     if (ts > 0.0) flags |= 1;
     double slack = 1e-11;
     int ok = 0;
+    if (ts > 0.0 && !valley_at(L, n, ts, vmax, ax, ay)) {
+        /* a single least-penetration velocity: the enumerated vertex itself
+           (projecting onto the relaxed set would only approximate it) */
+        *ox = ax;
+        *oy = ay;
+        ok = 1;
+    }
     for (int tries = 0; tries < 4 && !ok; ++tries, slack *= 100.0)
         ok = project_enum(L, n, t, vmax, vpx, vpy, slack, ox, oy);
     if (!ok) {
