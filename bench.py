@@ -300,6 +300,54 @@ def measure_batched(dev, flush, n_steps=50, tune=True):
              "candidates": [[a, bs, ms] for a, bs, ms in tuned.table]}}
 
 
+def measure_adjoint(dev, n_steps=40, ckpt_every=8, reps=5):
+    """The adjoint workload (4,000 pedestrians + 64 vehicles with 8 waypoints,
+    100 x 100 m): the checkpointing forward (orca_rollout) and the adjoint
+    (orca_adjoint: segment replays + reverse steps), CUDA events on the
+    launching stream, median of ``reps``."""
+    import torch
+
+    from paper_2008_11578_gb300 import api, scenes
+    from paper_2008_11578_gb300.adjoint import Rollout, workload_loss
+    s = scenes.waypoint_square()
+    roll = Rollout(s, n_steps, ckpt_every, device=dev)
+    stream = torch.cuda.current_stream()
+    d = torch.zeros((n_steps, s.n, 2), dtype=torch.float32, device=dev)
+    goal = torch.as_tensor(s.goal, device=dev)
+    veh = torch.as_tensor(s.type == 1, device=dev)
+    fw, bw, plain = [], [], []
+    for r in range(reps + 1):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        roll.forward_raw(d)
+        e[1].record(stream)
+        pos_T = roll.ds.pos.clone().requires_grad_(True)
+        vt = roll.vel_traj.clone().requires_grad_(True)
+        gp, gv = torch.autograd.grad(workload_loss(pos_T, vt, goal, veh), [pos_T, vt])
+        e[2].record(stream)
+        roll.backward_raw(d, gp, gv)
+        e[3].record(stream)
+        roll.reset()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        roll.ds.step(n_steps, d)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        if r > 0:                                   # the first round is warm-up
+            fw.append(e[0].elapsed_time(e[1]))
+            bw.append(e[2].elapsed_time(e[3]))
+            plain.append(p0.elapsed_time(p1))
+    f, b, pl = statistics.median(fw), statistics.median(bw), statistics.median(plain)
+    out = {"workload": "waypoint_square_4k", "agents": s.n, "vehicles": int((s.type == 1).sum()),
+           "steps": n_steps, "ckpt_every": ckpt_every, "forward_ms": f, "adjoint_ms": b,
+           "plain_steps_ms": pl, "adjoint_over_forward": b / f,
+           "forward_value": s.n * n_steps / (f / 1e3), "unit": METRIC,
+           "adjoint_launches": api.orca_adjoint_launch_count(roll.ds.handle, n_steps,
+                                                             ckpt_every)}
+    roll.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -424,6 +472,8 @@ def run_ours(args):
             "hbm_peak_gbs": peaks.get("hbm_gbs")}
     if not args.no_batched:
         line["batched"] = measure_batched(dev, flush)
+    if not args.no_adjoint:
+        line["adjoint"] = measure_adjoint(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, cfg)
     if rank == 0:
@@ -444,6 +494,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

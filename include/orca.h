@@ -214,6 +214,89 @@ int orca_scene_sync_status(orca_scene *scene);
 void orca_scene_destroy(orca_scene *scene);
 
 /*
+ * Record the velocity LP's active set of every agent in every following
+ * step (NULL to stop): act[N] uint32, caller order, packed as
+ *   bits 0-1   0 = projection of the preferred velocity onto the admissible
+ *              set, 1 = least-penetration vertex, 2 = projection onto the
+ *              mid-line of two exactly opposite half-planes (valley)
+ *   bit 2      the speed circle |v| = max_speed is active
+ *   bits 3-4   number of active half-planes (0-3)
+ *   bits 8-12, 16-20, 24-28   their constraint indices (positions in nbr)
+ *   bits 13/21/29   that half-plane was built on the cut-off circle
+ *   bits 14/22/30   that half-plane belongs to an overlapping pair
+ * The active set decides how the adjoint differentiates the LP.
+ */
+int orca_scene_set_debug_active(orca_scene *scene, uint32_t *act);
+
+/*
+ * ---------------------------------------------------------------------------
+ * Differentiable rollouts.  The paper runs the ORCA update forward only; the
+ * adjoint below is an addition of this library.  A rollout of n_steps steps
+ * maps the preferred-velocity offsets delta[t][i] (the vpref_delta of
+ * orca_step) and the waypoint table to the trajectory.  orca_adjoint
+ * returns the gradient of a scalar loss L from dL/dpos after the last step
+ * and dL/dvel after every step.  Each LP is differentiated through its
+ * active half-planes and speed circle (implicit function on the active set);
+ * neighbour sets, active sets, leg/cut-off choices and waypoint switches are
+ * held fixed (no gradient through discrete choices).  Memory: the state is
+ * checkpointed every ckpt_every steps and each segment is recomputed.
+ * ---------------------------------------------------------------------------
+ */
+
+/* Bytes of the caller-owned adjoint workspace of a rollout. */
+int orca_adjoint_workspace_bytes(const orca_scene *scene, int n_steps, int ckpt_every,
+                                 size_t *out_bytes);
+
+/*
+ * orca_step over n_steps steps that also stores checkpoints in adj_ws
+ * (device, 256-byte aligned, orca_adjoint_workspace_bytes bytes) and, when
+ * vel_traj != NULL, writes the velocity after every step into vel_traj
+ * (float2[n_steps * N], step-major, caller order).  The scene's pos, vel and
+ * wp_idx advance as with orca_step.
+ */
+int orca_rollout(orca_scene *scene, int n_steps, int ckpt_every, const float *vpref_delta,
+                 void *adj_ws, size_t adj_bytes, float *vel_traj, void *stream);
+
+/*
+ * Gradient of L through the last orca_rollout of this scene (same n_steps,
+ * ckpt_every, vpref_delta and adj_ws, else ORCA_ERR_INVALID_ARG; the scene's
+ * current state is not used).  Inputs (device, caller order):
+ *   dl_dpos          float2[N]  dL/dpos after the last step (required)
+ *   dl_dvel_traj     float2[n_steps * N] dL/d(velocity after step t), or NULL
+ * Outputs (device, overwritten, any may be NULL):
+ *   dl_dvpref_delta  float2[n_steps * N]
+ *   dl_dwaypoints    float2[n_routes * n_waypoints] (scene needs routes)
+ *   dl_dpos0, dl_dvel0  float2[N] gradient w.r.t. the rollout's start state
+ * Neighbour cotangents are summed with atomics, so the last bits of the
+ * result can vary between runs.
+ */
+int orca_adjoint(orca_scene *scene, int n_steps, int ckpt_every, const float *vpref_delta,
+                 void *adj_ws, size_t adj_bytes, const float *dl_dpos,
+                 const float *dl_dvel_traj, float *dl_dvpref_delta, float *dl_dwaypoints,
+                 float *dl_dpos0, float *dl_dvel0, void *stream);
+
+/*
+ * Vector-Jacobian product of ONE step at a given state, for callers that
+ * build their own reverse loops (or linearise along another trajectory).
+ * Inputs (device, caller order): the state at the step's start pos, vel
+ * (float2[N]) and wp_idx (uint8[N], required exactly when the scene has
+ * routes), vpref_delta (float2[N] or NULL), and the cotangents of the state
+ * after the step dl_dpos_next, dl_dvel_next (float2[N]; add any direct loss
+ * term on the new velocity to dl_dvel_next).  Outputs: dl_dpos, dl_dvel
+ * (float2[N], overwritten), dl_dvpref_delta (float2[N], overwritten, or
+ * NULL) and dl_dwaypoints (ACCUMULATED into, or NULL).  adj_ws must hold
+ * orca_adjoint_workspace_bytes(scene, 1, 1) bytes.  The scene's own state is
+ * not touched.
+ */
+int orca_step_vjp(orca_scene *scene, void *adj_ws, size_t adj_bytes, const float *pos,
+                  const float *vel, const uint8_t *wp_idx, const float *vpref_delta,
+                  const float *dl_dpos_next, const float *dl_dvel_next, float *dl_dpos,
+                  float *dl_dvel, float *dl_dvpref_delta, float *dl_dwaypoints, void *stream);
+
+/* Kernel launches of one orca_adjoint call (replays and adjoint kernels). */
+int orca_adjoint_launch_count(const orca_scene *scene, int n_steps, int ckpt_every);
+
+/*
  * ---------------------------------------------------------------------------
  * Batches: many independent scenes of uneven size advanced by one launch per
  * phase of the step.  The paper simulates one scene at a time (Sec. 4);

@@ -99,6 +99,12 @@ SIGNATURES = {
     "orca_scene_graph_launch": (_I, [_V, _V]),
     "orca_scene_sync_status": (_I, [_V]),
     "orca_scene_destroy": (None, [_V]),
+    "orca_scene_set_debug_active": (_I, [_V, _V]),
+    "orca_adjoint_workspace_bytes": (_I, [_V, _I, _I, ctypes.POINTER(ctypes.c_size_t)]),
+    "orca_rollout": (_I, [_V, _I, _I, _V, _V, ctypes.c_size_t, _V, _V]),
+    "orca_adjoint": (_I, [_V, _I, _I, _V, _V, ctypes.c_size_t, _V, _V, _V, _V, _V, _V, _V]),
+    "orca_adjoint_launch_count": (_I, [_V, _I, _I]),
+    "orca_step_vjp": (_I, [_V, _V, ctypes.c_size_t] + [_V] * 10 + [_V]),
     "orca_batch_workspace_bytes": (_I, [ctypes.POINTER(OrcaParams), _I,
                                        ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_size_t)]),

@@ -161,6 +161,51 @@ def orca_step_noalloc(params: OrcaParams, agents: OrcaAgents, n_steps: int,
                                              _stream_handle(stream), int(bool(synchronize))))
 
 
+def orca_scene_set_debug_active(handle, act=None):
+    """Record every agent's LP active set (uint32[N] on the device)."""
+    check(_lib.load().orca_scene_set_debug_active(handle, _ptr(act)),
+          "orca_scene_set_debug_active")
+
+
+def orca_adjoint_workspace_bytes(handle, n_steps: int, ckpt_every: int) -> int:
+    out = ctypes.c_size_t(0)
+    check(_lib.load().orca_adjoint_workspace_bytes(handle, int(n_steps), int(ckpt_every),
+                                                   ctypes.byref(out)),
+          "orca_adjoint_workspace_bytes")
+    return int(out.value)
+
+
+def orca_rollout(handle, n_steps: int, ckpt_every: int, vpref_delta, adj_ws, adj_bytes: int,
+                 vel_traj=None, stream=None):
+    check(_lib.load().orca_rollout(handle, int(n_steps), int(ckpt_every), _ptr(vpref_delta),
+                                   _ptr(adj_ws), int(adj_bytes), _ptr(vel_traj),
+                                   _stream_handle(stream)), "orca_rollout")
+
+
+def orca_adjoint(handle, n_steps: int, ckpt_every: int, vpref_delta, adj_ws, adj_bytes: int,
+                 dl_dpos, dl_dvel_traj=None, dl_dvpref_delta=None, dl_dwaypoints=None,
+                 dl_dpos0=None, dl_dvel0=None, stream=None):
+    check(_lib.load().orca_adjoint(handle, int(n_steps), int(ckpt_every), _ptr(vpref_delta),
+                                   _ptr(adj_ws), int(adj_bytes), _ptr(dl_dpos),
+                                   _ptr(dl_dvel_traj), _ptr(dl_dvpref_delta),
+                                   _ptr(dl_dwaypoints), _ptr(dl_dpos0), _ptr(dl_dvel0),
+                                   _stream_handle(stream)), "orca_adjoint")
+
+
+def orca_step_vjp(handle, adj_ws, adj_bytes: int, pos, vel, wp_idx, vpref_delta, dl_dpos_next,
+                  dl_dvel_next, dl_dpos, dl_dvel, dl_dvpref_delta=None, dl_dwaypoints=None,
+                  stream=None):
+    check(_lib.load().orca_step_vjp(handle, _ptr(adj_ws), int(adj_bytes), _ptr(pos), _ptr(vel),
+                                    _ptr(wp_idx), _ptr(vpref_delta), _ptr(dl_dpos_next),
+                                    _ptr(dl_dvel_next), _ptr(dl_dpos), _ptr(dl_dvel),
+                                    _ptr(dl_dvpref_delta), _ptr(dl_dwaypoints),
+                                    _stream_handle(stream)), "orca_step_vjp")
+
+
+def orca_adjoint_launch_count(handle, n_steps: int, ckpt_every: int) -> int:
+    return int(_lib.load().orca_adjoint_launch_count(handle, int(n_steps), int(ckpt_every)))
+
+
 def _params_array(params_list):
     arr = (OrcaParams * len(params_list))()
     for i, p in enumerate(params_list):
@@ -272,7 +317,10 @@ class DeviceScene:
         if debug:
             self.enable_debug()
 
-    def enable_debug(self):
+    def enable_debug(self, active=False):
+        """Per-agent diagnostics of the last step (``self.dbg``); with
+        ``active`` also the LP active set (``self.dbg["act"]``, int32 view of
+        the packed uint32 words)."""
         torch = _torch()
         n, k, dev = self.n, max(self.k, 1), self.device
         self.dbg = dict(cell=torch.full((n,), -1, dtype=torch.int32, device=dev),
@@ -281,6 +329,9 @@ class DeviceScene:
                         flags=torch.zeros(n, dtype=torch.uint8, device=dev),
                         tstar=torch.zeros(n, dtype=torch.float32, device=dev))
         orca_scene_set_debug(self.handle, **self.dbg)
+        if active:
+            self.dbg["act"] = torch.zeros(n, dtype=torch.int32, device=dev)
+            orca_scene_set_debug_active(self.handle, self.dbg["act"])
 
     def set_state(self, pos=None, vel=None, wp_idx=None):
         torch = _torch()

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "orca.h"
+#include "orca_adjoint.cuh"
 #include "orca_step_kernels.cuh"
 
 using namespace orca;
@@ -183,42 +184,43 @@ int kcap_for(int k) { return k <= 16 ? 16 : 32; }
 
 // More than 48 KB of dynamic shared memory needs an explicit opt-in, set
 // once per scene/batch on its device (outside any stream capture).
-template <class SRC>
-cudaError_t prepare_solve(int kcap, size_t smem) {
-    if (smem <= 48 * 1024) return cudaSuccess;
-    cudaError_t e = cudaSuccess;
-    if (kcap == 16) {
-        e = cudaFuncSetAttribute(solve_kernel<16, SRC, false>,
+template <int K, class SRC>
+cudaError_t prepare_solve_k(size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(solve_kernel<K, SRC, MODE_PLAIN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(solve_kernel<K, SRC, MODE_COUNT>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(solve_kernel<16, SRC, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    } else {
-        e = cudaFuncSetAttribute(solve_kernel<32, SRC, false>,
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(solve_kernel<K, SRC, MODE_RECORD>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(solve_kernel<32, SRC, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    }
     return e;
 }
 
 template <class SRC>
-void launch_solve(int kcap, bool count, int grid, int block, size_t smem, cudaStream_t st, int n,
+cudaError_t prepare_solve(int kcap, size_t smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return kcap == 16 ? prepare_solve_k<16, SRC>(smem) : prepare_solve_k<32, SRC>(smem);
+}
+
+template <class SRC>
+void launch_solve(int kcap, int mode, int grid, int block, size_t smem, cudaStream_t st, int n,
                   SRC src, const float2* pos, const float2* vel, const float* rad,
                   const uint8_t* typ, const int32_t* orig, const uint32_t* start, AgentIn ain,
                   const float2* vpd, float2* out_pos, float2* out_vel, DebugOut dbg,
                   unsigned long long* counters) {
-#define ORCA_SOLVE(K, C)                                                                   \
-    solve_kernel<K, SRC, C><<<grid, block, smem, st>>>(n, src, pos, vel, rad, typ, orig,    \
+#define ORCA_SOLVE(K, M)                                                                   \
+    solve_kernel<K, SRC, M><<<grid, block, smem, st>>>(n, src, pos, vel, rad, typ, orig,    \
                                                         start, ain, vpd, out_pos, out_vel, \
                                                         dbg, counters)
     if (kcap == 16) {
-        if (count) ORCA_SOLVE(16, true);
-        else ORCA_SOLVE(16, false);
+        if (mode == MODE_COUNT) ORCA_SOLVE(16, MODE_COUNT);
+        else if (mode == MODE_RECORD) ORCA_SOLVE(16, MODE_RECORD);
+        else ORCA_SOLVE(16, MODE_PLAIN);
     } else {
-        if (count) ORCA_SOLVE(32, true);
-        else ORCA_SOLVE(32, false);
+        if (mode == MODE_COUNT) ORCA_SOLVE(32, MODE_COUNT);
+        else if (mode == MODE_RECORD) ORCA_SOLVE(32, MODE_RECORD);
+        else ORCA_SOLVE(32, MODE_PLAIN);
     }
 #undef ORCA_SOLVE
 }
@@ -248,9 +250,22 @@ struct Pipeline {
 
 size_t solve_smem(const Pipeline& P) { return (size_t)P.kcap * P.block * sizeof(float4); }
 
-template <class SRC>
+// The solve variant and diagnostics of an ordinary step.
+struct SameDebug {
+    DebugOut d;
+    __host__ DebugOut operator()(int) const { return d; }
+};
+
+int step_mode(const Pipeline& P) {
+    if (P.counters != nullptr) return MODE_COUNT;
+    return P.dbg.act != nullptr ? MODE_RECORD : MODE_PLAIN;
+}
+
+// Enqueue load, n_steps steps and unload.  dbg_for(t) gives the solve
+// kernel's optional outputs of step t.
+template <class SRC, class DBG>
 void enqueue_steps(const Pipeline& P, SRC src, int n_steps, const float* vpref_delta,
-                   cudaStream_t st) {
+                   cudaStream_t st, DBG dbg_for, int mode) {
     const int n = P.n;
     const Buffers& B = P.buf;
     const orca_agents& A = P.agents;
@@ -283,9 +298,9 @@ void enqueue_steps(const Pipeline& P, SRC src, int n_steps, const float* vpref_d
         const float2* vpd =
             vpref_delta ? (const float2*)vpref_delta + (size_t)t * (size_t)n : nullptr;
         if (P.ev_begin) cudaEventRecord(P.ev_begin, st);
-        launch_solve(P.kcap, P.counters != nullptr, sgrid, sb, smem, st, n, src, B.pos1, B.vel1,
-                     B.rad[cur], B.typ[cur], B.orig[cur], B.start, ain, vpd, B.pos0, B.vel0,
-                     P.dbg, P.counters);
+        launch_solve(P.kcap, mode, sgrid, sb, smem, st, n, src, B.pos1, B.vel1, B.rad[cur],
+                     B.typ[cur], B.orig[cur], B.start, ain, vpd, B.pos0, B.vel0, dbg_for(t),
+                     P.counters);
         if (P.ev_end) cudaEventRecord(P.ev_end, st);
     }
     unload_kernel<<<gb, tb, 0, st>>>(n, B.orig[cur], B.pos0, B.vel0, (float2*)A.pos,
@@ -293,8 +308,12 @@ void enqueue_steps(const Pipeline& P, SRC src, int n_steps, const float* vpref_d
 }
 
 int run_steps(const Pipeline& P, int n_steps, const float* vpref_delta, cudaStream_t st) {
-    if (P.n_scenes == 0) enqueue_steps(P, OneScene{P.one}, n_steps, vpref_delta, st);
-    else enqueue_steps(P, ManyScenes{P.buf.scenes, P.buf.sid}, n_steps, vpref_delta, st);
+    const SameDebug dbg{P.dbg};
+    const int mode = step_mode(P);
+    if (P.n_scenes == 0) enqueue_steps(P, OneScene{P.one}, n_steps, vpref_delta, st, dbg, mode);
+    else
+        enqueue_steps(P, ManyScenes{P.buf.scenes, P.buf.sid}, n_steps, vpref_delta, st, dbg,
+                      mode);
     return cuda_status(cudaGetLastError());
 }
 
@@ -382,7 +401,8 @@ void init_pipeline(Pipeline& P, const orca_agents* agents, int ncells, int kcap,
     P.ws = (char*)workspace;
     P.buf = carve(P.ws, lay, n_scenes > 0);
     P.one = SceneDev{};
-    P.dbg = DebugOut{nullptr, nullptr, nullptr, nullptr, nullptr, k_stride};
+    P.dbg = DebugOut{};
+    P.dbg.k_stride = k_stride;
     P.ev_begin = P.ev_end = nullptr;
     P.counters = nullptr;
     P.graph = nullptr;
@@ -414,12 +434,121 @@ int check_batch(const orca_params* params, int n_scenes, const int* offsets, int
     return ORCA_OK;
 }
 
+// Adjoint workspace (caller owned): checkpoints of the rollout, the state
+// a segment is replayed from, what the replay records for each step of a
+// segment, and three rotating pairs of state cotangents.
+struct AdjLayout {
+    int n_ck;
+    size_t ck_pos, ck_vel, ck_wp;
+    size_t rp_pos, rp_vel, rp_wp;
+    size_t r_pos, r_vel, r_nbr, r_act, r_wp, r_vnew;
+    size_t bar_p[3], bar_v[3];
+    size_t total;
+};
+
+AdjLayout make_adj_layout(size_t n, int k, int n_steps, int K) {
+    AdjLayout L{};
+    L.n_ck = (n_steps + K - 1) / K;
+    const size_t ck = (size_t)std::max(L.n_ck, 1);
+    const size_t kk = (size_t)std::max(k, 1);
+    const size_t seg = (size_t)std::min(std::max(n_steps, 1), K);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    L.ck_pos = take(ck * n * 8);
+    L.ck_vel = take(ck * n * 8);
+    L.ck_wp = take(ck * n);
+    L.rp_pos = take(n * 8);
+    L.rp_vel = take(n * 8);
+    L.rp_wp = take(n);
+    L.r_pos = take(seg * n * 8);
+    L.r_vel = take(seg * n * 8);
+    L.r_nbr = take(seg * n * kk * 4);
+    L.r_act = take(seg * n * 4);
+    L.r_wp = take(seg * n);
+    L.r_vnew = take(seg * n * 8);
+    for (int b = 0; b < 3; ++b) {
+        L.bar_p[b] = take(n * 8);
+        L.bar_v[b] = take(n * 8);
+    }
+    L.total = o;
+    return L;
+}
+
 }  // namespace
 
 struct orca_scene {
     orca_params params;
     Pipeline p;
+    // the last orca_rollout: its length, checkpoint interval and workspace
+    int adj_steps;
+    int adj_every;
+    void* adj_ws;
 };
+
+namespace {
+
+int check_adjoint_args(const orca_scene* s, int n_steps, int ckpt_every, void* adj_ws,
+                       size_t adj_bytes, const float* vpref_delta) {
+    if (!s || n_steps < 0 || ckpt_every < 1) return ORCA_ERR_INVALID_ARG;
+    if (vpref_delta && !aligned(vpref_delta, 8)) return ORCA_ERR_INVALID_ARG;
+    const AdjLayout L = make_adj_layout((size_t)s->p.n, s->params.max_neighbors, n_steps,
+                                        ckpt_every);
+    if (!adj_ws || !aligned(adj_ws, kAlign) || adj_bytes < L.total) return ORCA_ERR_INVALID_ARG;
+    return ORCA_OK;
+}
+
+// Per-step outputs of the checkpointing forward: the new velocity of every
+// step, and the state at the start of every ckpt_every-th step.
+struct RolloutDebug {
+    DebugOut base;
+    float2* vel_traj;
+    float2* ck_pos;
+    float2* ck_vel;
+    uint8_t* ck_wp;
+    int n;
+    int every;
+    __host__ DebugOut operator()(int t) const {
+        DebugOut d = base;
+        d.vnew = vel_traj ? vel_traj + (size_t)t * n : nullptr;
+        if (t % every == 0) {
+            const size_t c = (size_t)(t / every) * n;
+            d.spos = ck_pos + c;
+            d.svel = ck_vel + c;
+            d.swp = ck_wp ? ck_wp + c : nullptr;
+        }
+        return d;
+    }
+};
+
+// Per-step records of a replayed segment for the adjoint kernel.
+struct ReplayDebug {
+    DebugOut base;
+    float2* r_pos;
+    float2* r_vel;
+    int32_t* r_nbr;
+    uint32_t* r_act;
+    uint8_t* r_wp;
+    float2* r_vnew;
+    int n;
+    int k;
+    __host__ DebugOut operator()(int t) const {
+        DebugOut d = base;
+        const size_t o = (size_t)t * n;
+        d.spos = r_pos + o;
+        d.svel = r_vel + o;
+        d.nbr = r_nbr + o * (size_t)k;
+        d.act = r_act + o;
+        d.wp_used = r_wp ? r_wp + o : nullptr;
+        d.vnew = r_vnew + o;
+        return d;
+    }
+};
+
+}  // namespace
 
 struct orca_batch {
     int n_scenes;
@@ -470,6 +599,9 @@ int orca_scene_create(const orca_params* params, const orca_agents* agents, void
     init_pipeline(s->p, agents, (int)ncells, kcap_for(params->max_neighbors),
                   params->block_size, 0, lay, workspace, params->max_neighbors);
     s->p.one = scene_dev(params, 0, s->p.n, 0);
+    s->adj_steps = -1;
+    s->adj_every = 0;
+    s->adj_ws = nullptr;
     if (cudaMemset(s->p.buf.err, 0, 16) != cudaSuccess || prepare(s->p) != ORCA_OK) {
         delete s;
         return ORCA_ERR_CUDA;
@@ -481,7 +613,11 @@ int orca_scene_create(const orca_params* params, const orca_agents* agents, void
 int orca_scene_set_debug(orca_scene* s, int32_t* cell, int32_t* nbr, int32_t* cnt,
                          uint8_t* flags, float* tstar) {
     if (!s) return ORCA_ERR_INVALID_ARG;
-    s->p.dbg = DebugOut{cell, nbr, cnt, flags, tstar, s->params.max_neighbors};
+    s->p.dbg.cell = cell;
+    s->p.dbg.nbr = nbr;
+    s->p.dbg.cnt = cnt;
+    s->p.dbg.flags = flags;
+    s->p.dbg.tstar = tstar;
     return ORCA_OK;
 }
 
@@ -530,6 +666,216 @@ void orca_scene_destroy(orca_scene* s) {
     if (!s) return;
     drop_graph(s->p);
     delete s;
+}
+
+int orca_scene_set_debug_active(orca_scene* s, uint32_t* act) {
+    if (!s || (act && !aligned(act, 4))) return ORCA_ERR_INVALID_ARG;
+    s->p.dbg.act = act;
+    return ORCA_OK;
+}
+
+// ------------------------------------------------------------- adjoint ----
+
+int orca_adjoint_workspace_bytes(const orca_scene* s, int n_steps, int ckpt_every,
+                                 size_t* out_bytes) {
+    if (!s || !out_bytes || n_steps < 0 || ckpt_every < 1) return ORCA_ERR_INVALID_ARG;
+    *out_bytes =
+        make_adj_layout((size_t)s->p.n, s->params.max_neighbors, n_steps, ckpt_every).total;
+    return ORCA_OK;
+}
+
+int orca_rollout(orca_scene* s, int n_steps, int ckpt_every, const float* vpref_delta,
+                 void* adj_ws, size_t adj_bytes, float* vel_traj, void* stream) {
+    int st = check_adjoint_args(s, n_steps, ckpt_every, adj_ws, adj_bytes, vpref_delta);
+    if (st != ORCA_OK) return st;
+    if (vel_traj && !aligned(vel_traj, 8)) return ORCA_ERR_INVALID_ARG;
+    s->adj_steps = -1;
+    const int n = s->p.n;
+    if (n > 0 && n_steps > 0) {
+        const AdjLayout L = make_adj_layout((size_t)n, s->params.max_neighbors, n_steps,
+                                            ckpt_every);
+        char* w = (char*)adj_ws;
+        RolloutDebug dbg{DebugOut{}, (float2*)vel_traj, (float2*)(w + L.ck_pos),
+                         (float2*)(w + L.ck_vel),
+                         s->p.agents.route ? (uint8_t*)(w + L.ck_wp) : nullptr, n, ckpt_every};
+        dbg.base.k_stride = s->params.max_neighbors;
+        enqueue_steps(s->p, OneScene{s->p.one}, n_steps, vpref_delta, (cudaStream_t)stream, dbg,
+                      MODE_PLAIN);
+        st = cuda_status(cudaGetLastError());
+        if (st != ORCA_OK) return st;
+    }
+    s->adj_steps = n_steps;
+    s->adj_every = ckpt_every;
+    s->adj_ws = adj_ws;
+    return ORCA_OK;
+}
+
+int orca_adjoint(orca_scene* s, int n_steps, int ckpt_every, const float* vpref_delta,
+                 void* adj_ws, size_t adj_bytes, const float* dl_dpos, const float* dl_dvel_traj,
+                 float* dl_dvpref_delta, float* dl_dwaypoints, float* dl_dpos0, float* dl_dvel0,
+                 void* stream) {
+    int st = check_adjoint_args(s, n_steps, ckpt_every, adj_ws, adj_bytes, vpref_delta);
+    if (st != ORCA_OK) return st;
+    if (s->adj_steps != n_steps || s->adj_every != ckpt_every || s->adj_ws != adj_ws)
+        return ORCA_ERR_INVALID_ARG;
+    const int n = s->p.n;
+    if (n > 0 && !dl_dpos) return ORCA_ERR_INVALID_ARG;
+    const void* ptrs[] = {dl_dpos, dl_dvel_traj, dl_dvpref_delta, dl_dwaypoints, dl_dpos0,
+                          dl_dvel0};
+    for (const void* q : ptrs)
+        if (q && !aligned(q, 8)) return ORCA_ERR_INVALID_ARG;
+    const orca_agents& A = s->p.agents;
+    if (dl_dwaypoints && !A.route) return ORCA_ERR_INVALID_ARG;
+    cudaStream_t stm = (cudaStream_t)stream;
+    const size_t nb = (size_t)n * 8;
+    if (dl_dwaypoints &&
+        cudaMemsetAsync(dl_dwaypoints, 0, (size_t)A.n_routes * A.n_waypoints * 8, stm) !=
+            cudaSuccess)
+        return ORCA_ERR_CUDA;
+    if (n == 0) return ORCA_OK;
+    if (n_steps == 0) {
+        if (dl_dpos0 && cudaMemcpyAsync(dl_dpos0, dl_dpos, nb, cudaMemcpyDeviceToDevice, stm))
+            return ORCA_ERR_CUDA;
+        if (dl_dvel0 && cudaMemsetAsync(dl_dvel0, 0, nb, stm)) return ORCA_ERR_CUDA;
+        return ORCA_OK;
+    }
+    const int k = s->params.max_neighbors;
+    const AdjLayout L = make_adj_layout((size_t)n, k, n_steps, ckpt_every);
+    char* w = (char*)adj_ws;
+    float2* bp[3] = {(float2*)(w + L.bar_p[0]), (float2*)(w + L.bar_p[1]),
+                     (float2*)(w + L.bar_p[2])};
+    float2* bv[3] = {(float2*)(w + L.bar_v[0]), (float2*)(w + L.bar_v[1]),
+                     (float2*)(w + L.bar_v[2])};
+    bool ok = cudaMemcpyAsync(bp[0], dl_dpos, nb, cudaMemcpyDeviceToDevice, stm) == cudaSuccess &&
+              cudaMemsetAsync(bv[0], 0, nb, stm) == cudaSuccess &&
+              cudaMemsetAsync(bp[1], 0, nb, stm) == cudaSuccess &&
+              cudaMemsetAsync(bv[1], 0, nb, stm) == cudaSuccess;
+    if (!ok) return ORCA_ERR_CUDA;
+
+    // the replay pipeline: the scene's kernels over the replay state arrays
+    Pipeline R = s->p;
+    R.agents.pos = (float*)(w + L.rp_pos);
+    R.agents.vel = (float*)(w + L.rp_vel);
+    if (A.route) R.agents.wp_idx = (uint8_t*)(w + L.rp_wp);
+    R.ev_begin = R.ev_end = nullptr;
+    R.counters = nullptr;
+    R.graph = nullptr;
+    ReplayDebug rec{DebugOut{}, (float2*)(w + L.r_pos), (float2*)(w + L.r_vel),
+                    (int32_t*)(w + L.r_nbr), (uint32_t*)(w + L.r_act),
+                    A.route ? (uint8_t*)(w + L.r_wp) : nullptr, (float2*)(w + L.r_vnew), n,
+                    std::max(k, 1)};
+    rec.base.k_stride = std::max(k, 1);
+    const AgentIn ain{(const float2*)A.goal, A.max_speed, A.route, (const float2*)A.waypoints,
+                      A.n_waypoints, A.wp_idx};
+    int nx = 0, cu = 1, sp = 2;
+    const int ab = 128, ag = (n + ab - 1) / ab;
+    for (int seg = L.n_ck - 1; seg >= 0; --seg) {
+        const int t0 = seg * ckpt_every;
+        const int t1 = std::min(n_steps, t0 + ckpt_every);
+        const size_t c = (size_t)seg * n;
+        ok = cudaMemcpyAsync(R.agents.pos, (float2*)(w + L.ck_pos) + c, nb,
+                             cudaMemcpyDeviceToDevice, stm) == cudaSuccess &&
+             cudaMemcpyAsync(R.agents.vel, (float2*)(w + L.ck_vel) + c, nb,
+                             cudaMemcpyDeviceToDevice, stm) == cudaSuccess &&
+             (!A.route || cudaMemcpyAsync(R.agents.wp_idx, (uint8_t*)(w + L.ck_wp) + c, n,
+                                          cudaMemcpyDeviceToDevice, stm) == cudaSuccess);
+        if (!ok) return ORCA_ERR_CUDA;
+        const float* vpd0 = vpref_delta ? vpref_delta + (size_t)t0 * n * 2 : nullptr;
+        enqueue_steps(R, OneScene{R.one}, t1 - t0, vpd0, stm, rec, MODE_RECORD);
+        for (int t = t1 - 1; t >= t0; --t) {
+            const size_t o = (size_t)(t - t0) * n;
+            const size_t tn = (size_t)t * n;
+            // the kernel reads the scene's radius/type in caller order
+            adjoint_kernel<<<ag, ab, 0, stm>>>(
+                n, s->p.one, rec.r_pos + o, rec.r_vel + o, A.radius, A.type,
+                rec.r_nbr + o * rec.k, rec.k, rec.r_act + o, rec.r_wp ? rec.r_wp + o : nullptr,
+                rec.r_vnew + o, ain, vpref_delta ? (const float2*)vpref_delta + tn : nullptr,
+                bp[nx], bv[nx], dl_dvel_traj ? (const float2*)dl_dvel_traj + tn : nullptr,
+                bp[cu], bv[cu], bp[sp], bv[sp],
+                dl_dvpref_delta ? (float2*)dl_dvpref_delta + tn : nullptr,
+                (float2*)dl_dwaypoints);
+            const int old_nx = nx;
+            nx = cu;
+            cu = sp;
+            sp = old_nx;
+        }
+    }
+    if (dl_dpos0 &&
+        cudaMemcpyAsync(dl_dpos0, bp[nx], nb, cudaMemcpyDeviceToDevice, stm) != cudaSuccess)
+        return ORCA_ERR_CUDA;
+    if (dl_dvel0 &&
+        cudaMemcpyAsync(dl_dvel0, bv[nx], nb, cudaMemcpyDeviceToDevice, stm) != cudaSuccess)
+        return ORCA_ERR_CUDA;
+    return cuda_status(cudaGetLastError());
+}
+
+int orca_step_vjp(orca_scene* s, void* adj_ws, size_t adj_bytes, const float* pos,
+                  const float* vel, const uint8_t* wp_idx, const float* vpref_delta,
+                  const float* dl_dpos_next, const float* dl_dvel_next, float* dl_dpos,
+                  float* dl_dvel, float* dl_dvpref_delta, float* dl_dwaypoints, void* stream) {
+    int st = check_adjoint_args(s, 1, 1, adj_ws, adj_bytes, vpref_delta);
+    if (st != ORCA_OK) return st;
+    const int n = s->p.n;
+    if (n == 0) return ORCA_OK;
+    const orca_agents& A = s->p.agents;
+    const void* ptrs[] = {pos, vel, dl_dpos_next, dl_dvel_next, dl_dpos, dl_dvel,
+                          dl_dvpref_delta, dl_dwaypoints};
+    for (const void* q : ptrs)
+        if (q && !aligned(q, 8)) return ORCA_ERR_INVALID_ARG;
+    if (!pos || !vel || !dl_dpos_next || !dl_dvel_next || !dl_dpos || !dl_dvel)
+        return ORCA_ERR_INVALID_ARG;
+    if ((A.route != nullptr) != (wp_idx != nullptr)) return ORCA_ERR_INVALID_ARG;
+    if (dl_dwaypoints && !A.route) return ORCA_ERR_INVALID_ARG;
+    cudaStream_t stm = (cudaStream_t)stream;
+    const int k = s->params.max_neighbors;
+    const AdjLayout L = make_adj_layout((size_t)n, k, 1, 1);
+    char* w = (char*)adj_ws;
+    const size_t nb = (size_t)n * 8;
+    Pipeline R = s->p;
+    R.agents.pos = (float*)(w + L.rp_pos);
+    R.agents.vel = (float*)(w + L.rp_vel);
+    if (A.route) R.agents.wp_idx = (uint8_t*)(w + L.rp_wp);
+    R.ev_begin = R.ev_end = nullptr;
+    R.counters = nullptr;
+    R.graph = nullptr;
+    bool ok = cudaMemcpyAsync(R.agents.pos, pos, nb, cudaMemcpyDeviceToDevice, stm) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(R.agents.vel, vel, nb, cudaMemcpyDeviceToDevice, stm) ==
+                  cudaSuccess &&
+              (!A.route || cudaMemcpyAsync(R.agents.wp_idx, wp_idx, n,
+                                           cudaMemcpyDeviceToDevice, stm) == cudaSuccess);
+    float2* bp[3] = {(float2*)(w + L.bar_p[0]), (float2*)(w + L.bar_p[1]),
+                     (float2*)(w + L.bar_p[2])};
+    float2* bv[3] = {(float2*)(w + L.bar_v[0]), (float2*)(w + L.bar_v[1]),
+                     (float2*)(w + L.bar_v[2])};
+    ok = ok && cudaMemsetAsync(bp[1], 0, nb, stm) == cudaSuccess &&
+         cudaMemsetAsync(bv[1], 0, nb, stm) == cudaSuccess;
+    if (!ok) return ORCA_ERR_CUDA;
+    ReplayDebug rec{DebugOut{}, (float2*)(w + L.r_pos), (float2*)(w + L.r_vel),
+                    (int32_t*)(w + L.r_nbr), (uint32_t*)(w + L.r_act),
+                    A.route ? (uint8_t*)(w + L.r_wp) : nullptr, (float2*)(w + L.r_vnew), n,
+                    std::max(k, 1)};
+    rec.base.k_stride = std::max(k, 1);
+    enqueue_steps(R, OneScene{R.one}, 1, vpref_delta, stm, rec, MODE_RECORD);
+    const AgentIn ain{(const float2*)A.goal, A.max_speed, A.route, (const float2*)A.waypoints,
+                      A.n_waypoints, A.wp_idx};
+    const int ab = 128, ag = (n + ab - 1) / ab;
+    adjoint_kernel<<<ag, ab, 0, stm>>>(
+        n, s->p.one, rec.r_pos, rec.r_vel, A.radius, A.type, rec.r_nbr, rec.k, rec.r_act,
+        rec.r_wp, rec.r_vnew, ain, (const float2*)vpref_delta, (const float2*)dl_dpos_next,
+        (const float2*)dl_dvel_next, nullptr, bp[1], bv[1], bp[2], bv[2],
+        (float2*)dl_dvpref_delta, (float2*)dl_dwaypoints);
+    ok = cudaMemcpyAsync(dl_dpos, bp[1], nb, cudaMemcpyDeviceToDevice, stm) == cudaSuccess &&
+         cudaMemcpyAsync(dl_dvel, bv[1], nb, cudaMemcpyDeviceToDevice, stm) == cudaSuccess;
+    if (!ok) return ORCA_ERR_CUDA;
+    return cuda_status(cudaGetLastError());
+}
+
+int orca_adjoint_launch_count(const orca_scene* s, int n_steps, int ckpt_every) {
+    if (!s || n_steps < 0 || ckpt_every < 1) return -1;
+    if (s->p.n == 0 || n_steps == 0) return 0;
+    const int n_ck = (n_steps + ckpt_every - 1) / ckpt_every;
+    return n_ck * 2 + 6 * n_steps + n_steps;   // replays (load/unload + steps) + adjoint kernels
 }
 
 // ------------------------------------------------------------- batches ----
@@ -592,7 +938,11 @@ int orca_batch_create(const orca_params* params, int n_scenes, const int* offset
 int orca_batch_set_debug(orca_batch* b, int32_t* cell, int32_t* nbr, int32_t* cnt,
                          uint8_t* flags, float* tstar) {
     if (!b) return ORCA_ERR_INVALID_ARG;
-    b->p.dbg = DebugOut{cell, nbr, cnt, flags, tstar, b->kmax};
+    b->p.dbg.cell = cell;
+    b->p.dbg.nbr = nbr;
+    b->p.dbg.cnt = cnt;
+    b->p.dbg.flags = flags;
+    b->p.dbg.tstar = tstar;
     return ORCA_OK;
 }
 

@@ -56,6 +56,10 @@ struct AgentIn {
     uint8_t* __restrict__ wp_idx;          // may be null when route is null
 };
 
+// Optional per-agent outputs of the solve kernel, caller order, any of them
+// null.  The first group is diagnostics; the second records what the adjoint
+// needs: the state at step start, the waypoint index before and after the
+// advance, the new velocity and the LP's active set (solve MODE_RECORD only).
 struct DebugOut {
     int32_t* cell;
     int32_t* nbr;
@@ -63,7 +67,16 @@ struct DebugOut {
     uint8_t* flags;
     float* tstar;
     int k_stride;
+    float2* spos;
+    float2* svel;
+    uint8_t* swp;
+    uint8_t* wp_used;
+    float2* vnew;
+    uint32_t* act;
 };
+
+// Variants of the solve kernel: plain, with work tallies, with the active set
+constexpr int MODE_PLAIN = 0, MODE_COUNT = 1, MODE_RECORD = 2;
 
 // Work tallies of the counting variant of the solve kernel:
 // [0] candidate key tests, [1] ORCA lines built, [2] LP pair evaluations

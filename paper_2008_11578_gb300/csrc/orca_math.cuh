@@ -56,11 +56,13 @@ __device__ __forceinline__ bool leg_left(float pax, float pay, float pbx, float 
 // disc; u runs from w_rel to its closest boundary point.  Overlapping pairs
 // use the cut-off construction with tau replaced by dt.  The line passes
 // through v_A + f u; its admissible side is left of the unit direction d.
-// Returned as (P_x, P_y, d_x, d_y).
+// Returned as (P_x, P_y, d_x, d_y); cap reports whether a non-overlapping
+// pair took the cut-off circle (true) or a leg (false).
 __device__ __forceinline__ float4 orca_line(float pax, float pay, float vax, float vay,
                                             float ra, float pbx, float pby, float vbx,
                                             float vby, float rb, float f, float inv_tau,
-                                            float inv_dt, bool overlap) {
+                                            float inv_dt, bool overlap, bool& cap) {
+    cap = false;
     float qx = pbx - pax, qy = pby - pay;
     float wrx = vax - vbx, wry = vay - vby;
     float rho = ra + rb;
@@ -72,6 +74,7 @@ __device__ __forceinline__ float4 orca_line(float pax, float pay, float vax, flo
         float rho2 = rho * rho;
         if (wq < 0.0f && wq * wq > rho2 * ww) {
             // cut-off circle
+            cap = true;
             float wl = sqrtf(ww);
             float hx = wx / wl, hy = wy / wl;
             dx = hy;
@@ -128,6 +131,39 @@ __device__ __forceinline__ float penetration(float4 L, float vx, float vy) {
 }
 
 // ---------------------------------------------------------------------------
+// Active set of the velocity LP, packed in 32 bits for the adjoint:
+//   bits 0-1   kind: ACT_PROJ   projection of v_pref onto the admissible set
+//                    ACT_VERTEX least-penetration vertex (no v_pref term)
+//                    ACT_VALLEY projection of v_pref onto a valley mid-line
+//   bit 2      the speed circle |v| = vmax is active
+//   bits 3-4   number of active lines (0-3)
+//   bits 8-12, 16-20, 24-28   constraint indices of active lines a, b, c
+//   bits 13/21/29   line a/b/c was built by the cut-off circle construction
+//   bits 14/22/30   line a/b/c is an overlapping pair
+// The solver fills kind, circle and indices; the solve kernel adds the
+// construction bits of the active lines.
+// ---------------------------------------------------------------------------
+enum : uint32_t { ACT_PROJ = 0u, ACT_VERTEX = 1u, ACT_VALLEY = 2u };
+
+__host__ __device__ __forceinline__ uint32_t act_pack(uint32_t kind, bool circle, int nl, int a,
+                                                      int b, int c) {
+    return kind | (circle ? 4u : 0u) | ((uint32_t)nl << 3) | ((uint32_t)(a & 31) << 8) |
+           ((uint32_t)(b & 31) << 16) | ((uint32_t)(c & 31) << 24);
+}
+__host__ __device__ __forceinline__ uint32_t act_kind(uint32_t a) { return a & 3u; }
+__host__ __device__ __forceinline__ bool act_circle(uint32_t a) { return (a >> 2) & 1u; }
+__host__ __device__ __forceinline__ int act_nlines(uint32_t a) { return (int)((a >> 3) & 3u); }
+__host__ __device__ __forceinline__ int act_line(uint32_t a, int m) {
+    return (int)((a >> (8 + 8 * m)) & 31u);
+}
+__host__ __device__ __forceinline__ bool act_cap(uint32_t a, int m) {
+    return (a >> (13 + 8 * m)) & 1u;
+}
+__host__ __device__ __forceinline__ bool act_overlap(uint32_t a, int m) {
+    return (a >> (14 + 8 * m)) & 1u;
+}
+
+// ---------------------------------------------------------------------------
 // Velocity LP (paper Sec. 3, LP paragraphs).  Lines live in shared memory at
 // L[i * stride].  The objective is the Euclidean distance to v_pref, so the
 // incremental scheme is exact: when the current optimum violates line i, the
@@ -137,15 +173,18 @@ __device__ __forceinline__ float penetration(float4 L, float vx, float vy) {
 
 // 1D problem on line i: the point of line i closest to v_pref that keeps
 // lines 0..i-1 and the disc.  Returns false when that set is empty.
+// bound: the constraint that binds the result on line i (-2 none, -1 the
+// speed circle, j >= 0 line j).
 __device__ __forceinline__ bool lp1_project(const float4* __restrict__ L, int stride, int i,
                                             float vmax, float vpx, float vpy, float& ox,
-                                            float& oy, int& work) {
+                                            float& oy, int& work, int& bound) {
     float4 li = L[i * stride];
     float dot = li.x * li.z + li.y * li.w;
     float disc = dot * dot + vmax * vmax - (li.x * li.x + li.y * li.y);
     if (disc < 0.0f) return false;
     float sq = sqrtf(disc);
     float tl = -dot - sq, tr = -dot + sq;
+    int jl = -1, jr = -1;
     for (int j = 0; j < i; ++j) {
         ++work;
         float4 lj = L[j * stride];
@@ -156,12 +195,18 @@ __device__ __forceinline__ bool lp1_project(const float4* __restrict__ L, int st
             continue;
         }
         float t = num / den;
-        if (den > 0.0f) tr = fminf(tr, t);
-        else tl = fmaxf(tl, t);
+        if (den > 0.0f) {
+            if (t < tr) jr = j;
+            tr = fminf(tr, t);
+        } else {
+            if (t > tl) jl = j;
+            tl = fmaxf(tl, t);
+        }
         if (tl > tr) return false;
     }
-    float t = li.z * (vpx - li.x) + li.w * (vpy - li.y);
-    t = fminf(fmaxf(t, tl), tr);
+    float t0 = li.z * (vpx - li.x) + li.w * (vpy - li.y);
+    float t = fminf(fmaxf(t0, tl), tr);
+    bound = (t0 > tr) ? jr : ((t0 < tl) ? jl : -2);
     ox = li.x + t * li.z;
     oy = li.y + t * li.w;
     return true;
@@ -172,23 +217,28 @@ __device__ __forceinline__ bool lp1_project(const float4* __restrict__ L, int st
 // the optimum of the lines before it).
 __device__ __forceinline__ int lp2_project(const float4* __restrict__ L, int stride, int n,
                                            float vmax, float vpx, float vpy, float& vx,
-                                           float& vy, int& work) {
+                                           float& vy, int& work, uint32_t& act) {
     float vp2 = vpx * vpx + vpy * vpy;
     if (vp2 > vmax * vmax) {
         float s = vmax / sqrtf(vp2);
         vx = vpx * s;
         vy = vpy * s;
+        act = act_pack(ACT_PROJ, true, 0, 0, 0, 0);
     } else {
         vx = vpx;
         vy = vpy;
+        act = act_pack(ACT_PROJ, false, 0, 0, 0, 0);
     }
     for (int i = 0; i < n; ++i) {
         float4 li = L[i * stride];
         if (penetration(li, vx, vy) > 0.0f) {
             float ox, oy;
-            if (!lp1_project(L, stride, i, vmax, vpx, vpy, ox, oy, work)) return i;
+            int bound;
+            if (!lp1_project(L, stride, i, vmax, vpx, vpy, ox, oy, work, bound)) return i;
             vx = ox;
             vy = oy;
+            act = bound >= 0 ? act_pack(ACT_PROJ, false, 2, i, bound, 0)
+                             : act_pack(ACT_PROJ, bound == -1, 1, i, 0, 0);
         }
     }
     return n;
@@ -221,16 +271,18 @@ __device__ __forceinline__ bool bisector(float4 li, float4 lj, float4& b) {
 // the disc is a 2D LP with the linear objective n_i . v.  Writes the point.
 __device__ __forceinline__ float lp3_min_penetration(const float4* __restrict__ L, int stride,
                                                      int n, float vmax, float& vx, float& vy,
-                                                     int& work) {
+                                                     int& work, uint32_t& act) {
     float4 l0 = L[0];
     vx = -l0.w * vmax;
     vy = l0.z * vmax;
+    act = act_pack(ACT_VERTEX, true, 1, 0, 0, 0);
     float t = penetration(l0, vx, vy);
     for (int i = 1; i < n; ++i) {
         float4 li = L[i * stride];
         if (penetration(li, vx, vy) <= t) continue;
         float nix = -li.w, niy = li.z;   // objective: maximise n_i . v
         float cx = vmax * nix, cy = vmax * niy;
+        uint32_t ai = act_pack(ACT_VERTEX, true, 1, i, 0, 0);
         for (int j = 0; j < i; ++j) {
             ++work;
             float4 bj;
@@ -241,6 +293,7 @@ __device__ __forceinline__ float lp3_min_penetration(const float4* __restrict__ 
             if (disc < 0.0f) continue;
             float sq = sqrtf(disc);
             float tl = -dot - sq, tr = -dot + sq;
+            int kl = -1, kr = -1;
             bool ok = true;
             for (int jj = 0; jj < j; ++jj) {
                 work += 2;   // a bisector and a 1D bound
@@ -253,17 +306,27 @@ __device__ __forceinline__ float lp3_min_penetration(const float4* __restrict__ 
                     continue;
                 }
                 float tt = num / den;
-                if (den > 0.0f) tr = fminf(tr, tt);
-                else tl = fmaxf(tl, tt);
+                if (den > 0.0f) {
+                    if (tt < tr) kr = jj;
+                    tr = fminf(tr, tt);
+                } else {
+                    if (tt > tl) kl = jj;
+                    tl = fmaxf(tl, tt);
+                }
                 if (tl > tr) { ok = false; break; }
             }
             if (!ok) continue;   // empty only through rounding: keep the point
-            float tt = (nix * bj.z + niy * bj.w > 0.0f) ? tr : tl;
+            const bool right = nix * bj.z + niy * bj.w > 0.0f;
+            float tt = right ? tr : tl;
+            const int kb = right ? kr : kl;
             cx = bj.x + tt * bj.z;
             cy = bj.y + tt * bj.w;
+            ai = kb >= 0 ? act_pack(ACT_VERTEX, false, 3, i, j, kb)
+                         : act_pack(ACT_VERTEX, true, 2, i, j, 0);
         }
         vx = cx;
         vy = cy;
+        act = ai;
         t = penetration(li, vx, vy);
     }
     float tm = -CUDART_INF_F;
@@ -279,7 +342,7 @@ __device__ __forceinline__ float lp3_min_penetration(const float4* __restrict__ 
 __device__ __forceinline__ bool valley_tie_break(const float4* __restrict__ L, int stride,
                                                  int n, float t3, float vmax, float vpx,
                                                  float vpy, float v3x, float v3y, float& ox,
-                                                 float& oy, int& work) {
+                                                 float& oy, int& work, uint32_t& act) {
     const float atol = 1e-5f * (1.0f + fabsf(t3));
     int vi = -1, vj = -1;
     for (int i = 0; i < n && vi < 0; ++i) {
@@ -305,6 +368,7 @@ __device__ __forceinline__ bool valley_tie_break(const float4* __restrict__ L, i
     const float sq = sqrtf(disc);
     float tl = -dot - sq, tr = -dot + sq;
     const float T = t3 + 1e-6f * (1.0f + fabsf(t3));
+    int kl = -1, kr = -1;
     for (int k = 0; k < n; ++k) {
         if (k == vi || k == vj) continue;
         ++work;
@@ -317,12 +381,21 @@ __device__ __forceinline__ bool valley_tie_break(const float4* __restrict__ L, i
             continue;
         }
         const float s = num / den;
-        if (den > 0.0f) tr = fminf(tr, s);
-        else tl = fmaxf(tl, s);
+        if (den > 0.0f) {
+            if (s < tr) kr = k;
+            tr = fminf(tr, s);
+        } else {
+            if (s > tl) kl = k;
+            tl = fmaxf(tl, s);
+        }
     }
     if (tl > tr) return false;
-    float s = m.z * (vpx - m.x) + m.w * (vpy - m.y);
-    s = fminf(fmaxf(s, tl), tr);
+    const float s0 = m.z * (vpx - m.x) + m.w * (vpy - m.y);
+    const float s = fminf(fmaxf(s0, tl), tr);
+    const int kb = (s0 > tr) ? kr : ((s0 < tl) ? kl : -2);
+    act = kb >= 0   ? act_pack(ACT_VERTEX, false, 3, vi, vj, kb)
+          : kb == -1 ? act_pack(ACT_VERTEX, true, 2, vi, vj, 0)
+                     : act_pack(ACT_VALLEY, false, 2, vi, vj, 0);
     ox = m.x + s * m.z;
     oy = m.y + s * m.w;
     return true;
@@ -333,16 +406,17 @@ __device__ __forceinline__ bool valley_tie_break(const float4* __restrict__ L, i
 // the order given.  Returns 1 when the half-planes were infeasible.
 __device__ __forceinline__ int solve_velocity(const float4* __restrict__ L, int stride, int n,
                                               float vmax, float vpx, float vpy, float& vx,
-                                              float& vy, float& tstar, int& work) {
+                                              float& vy, float& tstar, int& work,
+                                              uint32_t& act) {
     tstar = 0.0f;
-    if (lp2_project(L, stride, n, vmax, vpx, vpy, vx, vy, work) == n) return 0;
+    if (lp2_project(L, stride, n, vmax, vpx, vpy, vx, vy, work, act) == n) return 0;
     float v3x, v3y;
-    const float t3 = lp3_min_penetration(L, stride, n, vmax, v3x, v3y, work);
+    const float t3 = lp3_min_penetration(L, stride, n, vmax, v3x, v3y, work, act);
     tstar = t3;
     vx = v3x;
     vy = v3y;
     float ox, oy;
-    if (valley_tie_break(L, stride, n, t3, vmax, vpx, vpy, v3x, v3y, ox, oy, work)) {
+    if (valley_tie_break(L, stride, n, t3, vmax, vpx, vpy, v3x, v3y, ox, oy, work, act)) {
         vx = ox;
         vy = oy;
     }

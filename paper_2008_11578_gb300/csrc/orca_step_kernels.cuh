@@ -173,9 +173,9 @@ __global__ void unload_kernel(int n, const int32_t* __restrict__ orig,
 // ----------------------------------------------------------------- solve ----
 // One thread per agent (sorted slot s).  Lines are kept in dynamic shared
 // memory, line i of thread t at [i * blockDim.x + t] (conflict-free float4).
-// COUNT = true adds work tallies (algorithmic FLOP accounting); the
-// increments are dead code in the COUNT = false instantiation.
-template <int KCAP, class SRC, bool COUNT>
+// MODE_COUNT adds work tallies (algorithmic FLOP accounting) and
+// MODE_RECORD the LP's active set; both are dead code in MODE_PLAIN.
+template <int KCAP, class SRC, int MODE>
 __global__ void __launch_bounds__(128)
 solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __restrict__ vel,
              const float* __restrict__ rad, const uint8_t* __restrict__ typ,
@@ -290,6 +290,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         const int rt = ain.route[o];
         if (rt >= 0) {
             int wi = ain.wp_idx[o];
+            if (dbg.swp != nullptr) dbg.swp[o] = (uint8_t)wi;
             const float2* W = ain.waypoints + (size_t)rt * ain.n_waypoints;
             float2 w = W[wi];
             float wdx = __fsub_rn(w.x, p.x), wdy = __fsub_rn(w.y, p.y);
@@ -297,6 +298,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
             if (wi < ain.n_waypoints - 1 && w2 <= __fmul_rn(r, r)) ++wi;
             g = W[wi];
             ain.wp_idx[o] = (uint8_t)wi;
+            if (dbg.wp_used != nullptr) dbg.wp_used[o] = (uint8_t)wi;
         }
     }
     float vpx = 0.0f, vpy = 0.0f;
@@ -332,6 +334,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
             if (i < k && i >= k - cnt) nb[k - 1 - i] = ko[i];
     }
     bool any_overlap = false;
+    uint32_t capbits = 0u, ovbits = 0u;   // per-line construction (MODE_RECORD)
     for (int i = 0; i < cnt; ++i) {
         const float4 e = L[i * stride];
         const int j = __float_as_int(e.y);
@@ -342,13 +345,20 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         const bool ov = e.x <= __fmul_rn(rs, rs);
         any_overlap |= ov;
         const float f = tb ? (ta ? sc.f11 : sc.f01) : (ta ? sc.f10 : sc.f00);
+        bool cap;
         L[i * stride] = orca_line(p.x, p.y, v.x, v.y, r, pj.x, pj.y, vj.x, vj.y, rj, f,
-                                  sc.inv_tau, sc.inv_dt, ov);
+                                  sc.inv_tau, sc.inv_dt, ov, cap);
+        if (MODE == MODE_RECORD) {
+            ovbits |= (ov ? 1u : 0u) << i;
+            capbits |= (cap ? 1u : 0u) << i;
+        }
     }
 
     // ---- velocity LP, least-penetration fallback ----
     float vx, vy, tstar;
-    const int infeasible = solve_velocity(L, stride, cnt, vmax, vpx, vpy, vx, vy, tstar, work);
+    uint32_t act = 0u;
+    const int infeasible =
+        solve_velocity(L, stride, cnt, vmax, vpx, vpy, vx, vy, tstar, work, act);
     const uint8_t flags = (uint8_t)(infeasible | (any_overlap ? 4 : 0));
 
     // ---- integrate ----
@@ -356,7 +366,20 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     out_pos[s] = make_float2(__fadd_rn(p.x, __fmul_rn(sc.dt, vx)),
                              __fadd_rn(p.y, __fmul_rn(sc.dt, vy)));
 
-    if (COUNT) {
+    if (dbg.spos != nullptr) dbg.spos[o] = p;
+    if (dbg.svel != nullptr) dbg.svel[o] = v;
+    if (dbg.vnew != nullptr) dbg.vnew[o] = make_float2(vx, vy);
+    if (MODE == MODE_RECORD && dbg.act != nullptr) {
+        const int nl = act_nlines(act);
+        for (int m = 0; m < nl; ++m) {
+            const int li = act_line(act, m);
+            act |= ((capbits >> li) & 1u) << (13 + 8 * m);
+            act |= ((ovbits >> li) & 1u) << (14 + 8 * m);
+        }
+        dbg.act[o] = act;
+    }
+
+    if (MODE == MODE_COUNT) {
         unsigned long long c[kNumCounters] = {(unsigned long long)n_cand,
                                               (unsigned long long)cnt,
                                               (unsigned long long)work,
