@@ -180,48 +180,38 @@ SceneDev scene_dev(const orca_params* p, int agent_off, int n, int cell_off) {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? ORCA_OK : ORCA_ERR_CUDA; }
 
-int kcap_for(int k) { return k <= 16 ? 16 : 32; }
+// float4 slots per thread: the neighbour list, then the lines
+int kcap_for(int k) { return std::max(k, 1); }
 
 // More than 48 KB of dynamic shared memory needs an explicit opt-in, set
 // once per scene/batch on its device (outside any stream capture).
-template <int K, class SRC>
-cudaError_t prepare_solve_k(size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(solve_kernel<K, SRC, MODE_PLAIN>,
+template <class SRC>
+cudaError_t prepare_solve(size_t smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(solve_kernel<SRC, MODE_PLAIN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(solve_kernel<K, SRC, MODE_COUNT>,
+        e = cudaFuncSetAttribute(solve_kernel<SRC, MODE_COUNT>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(solve_kernel<K, SRC, MODE_RECORD>,
+        e = cudaFuncSetAttribute(solve_kernel<SRC, MODE_RECORD>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return e;
 }
 
 template <class SRC>
-cudaError_t prepare_solve(int kcap, size_t smem) {
-    if (smem <= 48 * 1024) return cudaSuccess;
-    return kcap == 16 ? prepare_solve_k<16, SRC>(smem) : prepare_solve_k<32, SRC>(smem);
-}
-
-template <class SRC>
-void launch_solve(int kcap, int mode, int grid, int block, size_t smem, cudaStream_t st, int n,
-                  SRC src, const float2* pos, const float2* vel, const float* rad,
-                  const uint8_t* typ, const int32_t* orig, const uint32_t* start, AgentIn ain,
-                  const float2* vpd, float2* out_pos, float2* out_vel, DebugOut dbg,
+void launch_solve(int mode, int grid, int block, size_t smem, cudaStream_t st, int n, SRC src,
+                  const float2* pos, const float2* vel, const float* rad, const uint8_t* typ,
+                  const int32_t* orig, const uint32_t* start, AgentIn ain, const float2* vpd,
+                  float2* out_pos, float2* out_vel, DebugOut dbg,
                   unsigned long long* counters) {
-#define ORCA_SOLVE(K, M)                                                                   \
-    solve_kernel<K, SRC, M><<<grid, block, smem, st>>>(n, src, pos, vel, rad, typ, orig,    \
-                                                        start, ain, vpd, out_pos, out_vel, \
-                                                        dbg, counters)
-    if (kcap == 16) {
-        if (mode == MODE_COUNT) ORCA_SOLVE(16, MODE_COUNT);
-        else if (mode == MODE_RECORD) ORCA_SOLVE(16, MODE_RECORD);
-        else ORCA_SOLVE(16, MODE_PLAIN);
-    } else {
-        if (mode == MODE_COUNT) ORCA_SOLVE(32, MODE_COUNT);
-        else if (mode == MODE_RECORD) ORCA_SOLVE(32, MODE_RECORD);
-        else ORCA_SOLVE(32, MODE_PLAIN);
-    }
+#define ORCA_SOLVE(M)                                                                   \
+    solve_kernel<SRC, M><<<grid, block, smem, st>>>(n, src, pos, vel, rad, typ, orig,    \
+                                                     start, ain, vpd, out_pos, out_vel, \
+                                                     dbg, counters)
+    if (mode == MODE_COUNT) ORCA_SOLVE(MODE_COUNT);
+    else if (mode == MODE_RECORD) ORCA_SOLVE(MODE_RECORD);
+    else ORCA_SOLVE(MODE_PLAIN);
 #undef ORCA_SOLVE
 }
 
@@ -298,7 +288,7 @@ void enqueue_steps(const Pipeline& P, SRC src, int n_steps, const float* vpref_d
         const float2* vpd =
             vpref_delta ? (const float2*)vpref_delta + (size_t)t * (size_t)n : nullptr;
         if (P.ev_begin) cudaEventRecord(P.ev_begin, st);
-        launch_solve(P.kcap, mode, sgrid, sb, smem, st, n, src, B.pos1, B.vel1, B.rad[cur],
+        launch_solve(mode, sgrid, sb, smem, st, n, src, B.pos1, B.vel1, B.rad[cur],
                      B.typ[cur], B.orig[cur], B.start, ain, vpd, B.pos0, B.vel0, dbg_for(t),
                      P.counters);
         if (P.ev_end) cudaEventRecord(P.ev_end, st);
@@ -319,8 +309,8 @@ int run_steps(const Pipeline& P, int n_steps, const float* vpref_delta, cudaStre
 
 int prepare(const Pipeline& P) {
     const size_t smem = solve_smem(P);
-    cudaError_t e = P.n_scenes == 0 ? prepare_solve<OneScene>(P.kcap, smem)
-                                    : prepare_solve<ManyScenes>(P.kcap, smem);
+    cudaError_t e = P.n_scenes == 0 ? prepare_solve<OneScene>(smem)
+                                    : prepare_solve<ManyScenes>(smem);
     return cuda_status(e);
 }
 

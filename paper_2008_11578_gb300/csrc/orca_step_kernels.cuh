@@ -171,11 +171,12 @@ __global__ void unload_kernel(int n, const int32_t* __restrict__ orig,
 }
 
 // ----------------------------------------------------------------- solve ----
-// One thread per agent (sorted slot s).  Lines are kept in dynamic shared
-// memory, line i of thread t at [i * blockDim.x + t] (conflict-free float4).
+// One thread per agent (sorted slot s).  The neighbour list and then the
+// lines are kept in dynamic shared memory (k float4 slots per thread), slot i
+// of thread t at [i * blockDim.x + t] (conflict-free float4).
 // MODE_COUNT adds work tallies (algorithmic FLOP accounting) and
 // MODE_RECORD the LP's active set; both are dead code in MODE_PLAIN.
-template <int KCAP, class SRC, int MODE>
+template <class SRC, int MODE>
 __global__ void __launch_bounds__(128)
 solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __restrict__ vel,
              const float* __restrict__ rad, const uint8_t* __restrict__ typ,
@@ -198,18 +199,11 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     const int cy = cell_axis(p.y, sc.origin_y, sc.inv_cell, sc.ny);
 
     // ---- k nearest by (d^2, index), exact ring search over the grid ----
-    // The list holds k entries sorted by descending key; entry 0 is the
-    // current k-th nearest (the admission threshold), placeholders are +inf.
-    float kd[KCAP];
-    int ko[KCAP], ks[KCAP];
-#pragma unroll
-    for (int i = 0; i < KCAP; ++i) {
-        kd[i] = CUDART_INF_F;
-        ko[i] = INT_MAX;
-        ks[i] = -1;
-    }
+    // The list lives in the thread's line slots, sorted ascending by
+    // (d^2, original index): slot m = (d^2, sorted slot j, original index).
+    // An admitted candidate shifts only the entries behind it.
     const int k = sc.k;
-    float thr_d = CUDART_INF_F;
+    float thr_d = CUDART_INF_F;   // key of the k-th entry once the list is full
     int thr_o = INT_MAX;
     int cnt = 0;
     int n_cand = 0, work = 0;
@@ -248,27 +242,21 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                     if (d2 < R2 && d2 <= thr_d && j != s) {
                         const int oj = __ldg(orig + j);
                         if (d2 < thr_d || oj < thr_o) {
-                            // entry 0 (the current k-th key) leaves; the
-                            // candidate drops into place in the descending list
-                            bool placed = false;
-#pragma unroll
-                            for (int i = 0; i < KCAP; ++i) {
-                                if (i < k) {
-                                    const bool has_next = i + 1 < k;
-                                    const float nd = has_next ? kd[(i + 1) % KCAP] : -CUDART_INF_F;
-                                    const int no = has_next ? ko[(i + 1) % KCAP] : INT_MIN;
-                                    const int nj = has_next ? ks[(i + 1) % KCAP] : -1;
-                                    const bool shift = !placed && (nd > d2 || (nd == d2 && no > oj));
-                                    const bool put = !placed && !shift;
-                                    kd[i] = shift ? nd : (put ? d2 : kd[i]);
-                                    ko[i] = shift ? no : (put ? oj : ko[i]);
-                                    ks[i] = shift ? nj : (put ? j : ks[i]);
-                                    placed = placed || put;
-                                }
+                            int at = min(cnt, k - 1);   // a full list drops its last entry
+                            while (at > 0) {
+                                const float4 e = L[(at - 1) * stride];
+                                if (e.x < d2 || (e.x == d2 && __float_as_int(e.z) < oj)) break;
+                                L[at * stride] = e;
+                                --at;
                             }
+                            L[at * stride] =
+                                make_float4(d2, __int_as_float(j), __int_as_float(oj), 0.0f);
                             cnt = min(cnt + 1, k);
-                            thr_d = kd[0];
-                            thr_o = ko[0];
+                            if (cnt == k) {
+                                const float4 e = L[(k - 1) * stride];
+                                thr_d = e.x;
+                                thr_o = __float_as_int(e.z);
+                            }
                         }
                     }
                 }
@@ -318,20 +306,11 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     }
 
     // ---- one ORCA half-plane per neighbour (Sec. 3.1) ----
-    // The neighbour list leaves registers through the line slots (unrolled,
-    // constant indices); the line loop then runs rolled over shared memory.
-    // Constraint m is the m-th nearest: list entry k - 1 - m.
-#pragma unroll
-    for (int i = 0; i < KCAP; ++i) {
-        if (i < k && i >= k - cnt)
-            L[(k - 1 - i) * stride] = make_float4(kd[i], __int_as_float(ks[i]), 0.0f, 0.0f);
-    }
+    // Constraint m is the m-th nearest; its line replaces its list entry.
     if (dbg.nbr != nullptr) {
         int32_t* nb = dbg.nbr + (size_t)o * dbg.k_stride;
-        for (int m = cnt; m < dbg.k_stride; ++m) nb[m] = -1;
-#pragma unroll
-        for (int i = 0; i < KCAP; ++i)
-            if (i < k && i >= k - cnt) nb[k - 1 - i] = ko[i];
+        for (int m = 0; m < dbg.k_stride; ++m)
+            nb[m] = m < cnt ? __float_as_int(L[m * stride].z) : -1;
     }
     bool any_overlap = false;
     uint32_t capbits = 0u, ovbits = 0u;   // per-line construction (MODE_RECORD)
