@@ -57,7 +57,7 @@ __device__ __forceinline__ void orca_line_backward(
         // legs: d = sg (a, b) / |q|^2 with l = sqrt(|q|^2 - rho^2);
         // u = (w_rel . d) d - w_rel
         const float qq = qx * qx + qy * qy;
-        const float l = sqrtf(fmaxf(qq - rho * rho, 0.0f));
+        const float l = sqrtf(fmaxf(leg_l2(qx, qy, ra, rb, qq, rho * rho), 0.0f));
         const float iq = 1.0f / qq;
         const bool left = leg_left(pax, pay, pbx, pby, vax, vay, vbx, vby);
         const float sg = left ? 1.0f : -1.0f;

@@ -50,6 +50,21 @@ __device__ __forceinline__ bool leg_left(float pax, float pay, float pbx, float 
     return d64 > 0.0;
 }
 
+// Squared leg length |q|^2 - rho^2 of the velocity obstacle.  For a pair
+// close to touching, the FP32 difference of two nearly equal squares keeps
+// only a few correct bits (|q|^2 = 1.000038 against rho^2 = 1 loses three
+// digits), and the leg direction inherits that error; there it is redone in
+// FP64, where the products of the FP32 inputs are exact.
+__device__ __forceinline__ float leg_l2(float qx, float qy, float ra, float rb, float qq,
+                                        float rho2) {
+    float l2 = qq - rho2;
+    if (l2 < 0.015625f * qq) {
+        const double rho = (double)ra + (double)rb;
+        l2 = (float)((double)qx * qx + (double)qy * qy - rho * rho);
+    }
+    return l2;
+}
+
 // ORCA half-plane of agent A against neighbour B (paper Sec. 3.1, Fig. 1).
 // q = p_B - p_A, w_rel = v_A - v_B, rho = r_A + r_B.  The velocity obstacle is
 // the cone from the origin tangent to D(q/tau, rho/tau), cut off by that
@@ -85,7 +100,7 @@ __device__ __forceinline__ float4 orca_line(float pax, float pay, float vax, flo
         } else {
             // legs
             float qq = qx * qx + qy * qy;
-            float l = sqrtf(fmaxf(qq - rho2, 0.0f));
+            float l = sqrtf(fmaxf(leg_l2(qx, qy, ra, rb, qq, rho2), 0.0f));
             bool left = leg_left(pax, pay, pbx, pby, vax, vay, vbx, vby);
             float iq = 1.0f / qq;
             if (left) {
@@ -285,9 +300,16 @@ __device__ __forceinline__ float lp3_min_penetration(const float4* __restrict__ 
         uint32_t ai = act_pack(ACT_VERTEX, true, 1, i, 0, 0);
         for (int j = 0; j < i; ++j) {
             ++work;
+            const float4 lj = L[j * stride];
+            {
+                // is plane j above plane i at the current point?
+                // (n_j - n_i) . c < c_j - c_i, tested before the bisector is built
+                const float ax = li.w - lj.w, ay = lj.z - li.z;
+                const float beta = (lj.z * lj.y - lj.w * lj.x) - (li.z * li.y - li.w * li.x);
+                if (beta - (ax * cx + ay * cy) <= 0.0f) continue;
+            }
             float4 bj;
-            if (!bisector(li, L[j * stride], bj)) continue;
-            if (penetration(bj, cx, cy) <= 0.0f) continue;
+            if (!bisector(li, lj, bj)) continue;
             float dot = bj.x * bj.z + bj.y * bj.w;
             float disc = dot * dot + vmax * vmax - (bj.x * bj.x + bj.y * bj.y);
             if (disc < 0.0f) continue;
@@ -297,16 +319,20 @@ __device__ __forceinline__ float lp3_min_penetration(const float4* __restrict__ 
             bool ok = true;
             for (int jj = 0; jj < j; ++jj) {
                 work += 2;   // a bisector and a 1D bound
-                float4 bk;
-                if (!bisector(li, L[jj * stride], bk)) continue;
-                float den = bj.z * bk.w - bj.w * bk.z;
-                float num = bk.z * (bj.y - bk.y) - bk.w * (bj.x - bk.x);
+                // plane jj stays below plane i: (n_jj - n_i) . v >= c_jj - c_i,
+                // on bj at v = B + t e: t (a . e) >= (c_jj - c_i) - a . B
+                const float4 lk = L[jj * stride];
+                const float ax = li.w - lk.w, ay = lk.z - li.z;   // n_jj - n_i
+                if (ax * ax + ay * ay <= 1e-12f) continue;        // same direction
+                const float beta = (lk.z * lk.y - lk.w * lk.x) - (li.z * li.y - li.w * li.x);
+                const float den = ax * bj.z + ay * bj.w;
+                const float num = beta - (ax * bj.x + ay * bj.y);
                 if (den == 0.0f) {
-                    if (num < 0.0f) { ok = false; break; }
+                    if (num > 0.0f) { ok = false; break; }
                     continue;
                 }
-                float tt = num / den;
-                if (den > 0.0f) {
+                const float tt = num / den;
+                if (den < 0.0f) {
                     if (tt < tr) kr = jj;
                     tr = fminf(tr, tt);
                 } else {
