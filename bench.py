@@ -44,6 +44,13 @@ METRIC = "agent-steps/s"
 #   per agent: preferred velocity 10, disc clip 6, integration 4,
 #     1D set-ups amortised 10                                       = 30
 FLOPS_CAND, FLOPS_LINE, FLOPS_PAIR, FLOPS_AGENT = 5, 50, 10, 30
+# Algorithmic DRAM bytes of the binning phase:
+#   bin_count: position 8 read, key + slot 8 written, cell counter 8 (atomic
+#     read-modify-write)                                            = 24 / agent
+#   scatter: key, slot, cell start 12 + state 25 read, state 25 written = 62 / agent
+#   scan: count read 4, count cleared 4, start written 4; add pass start
+#     read + written 8                                              = 20 / cell
+BIN_BYTES_AGENT, BIN_BYTES_CELL = 24 + 62, 20
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -293,7 +300,7 @@ def measure_batched(dev, flush, n_steps=50, tune=True):
             "plain_loop_value": total * n_steps / (loop_ms / 1e3), "unit": METRIC,
             "graph_ms": graph_ms, "plain_loop_ms": loop_ms,
             "speedup_vs_plain_loop": loop_ms / graph_ms, "bitwise_equal": bool(same),
-            "graph_launches": 2 + 6 * n_steps, "plain_loop_launches": len(sl) * (2 + 6 * n_steps),
+            "graph_launches": 2 + 5 * n_steps, "plain_loop_launches": len(sl) * (2 + 5 * n_steps),
             "status": status,
             "autotune": None if tuned is None else
             {"alpha": tuned.alpha, "block_size": tuned.block_size,
@@ -353,7 +360,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2008_11578_gb300 import api, build
+    from paper_2008_11578_gb300 import api, autotune, build
 
     world, rank, local = _dist()
     if world > 1:
@@ -363,7 +370,15 @@ def run_ours(args):
     build()
     scene, cfg = _scene(args.workload)
     n = scene.n
-    ds = api.DeviceScene(scene, dev, cell_size=args.cell_size)
+    tuned = None
+    cell, block = args.cell_size, 0
+    if cell is None and not args.no_tune:
+        # launch shape only: every candidate computes bit-identical states
+        tuned = autotune.tune_scene(scene, dev, alphas=(1.0, 1.25, 1.5, 2.0), blocks=(64, 128),
+                                    steps=3, warmup=1)
+        cell = tuned.alpha * float(scene.params.cell_size)
+        block = tuned.block_size
+    ds = api.DeviceScene(scene, dev, cell_size=cell, block_size=block)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -382,6 +397,8 @@ def run_ours(args):
           for _ in range(args.steps)]
     sv = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    bv = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] \
         if "CUDA_VISIBLE_DEVICES" in os.environ else local
     barrier()
@@ -389,13 +406,16 @@ def run_ours(args):
         for k in range(args.steps):
             flush.zero_()
             api.orca_scene_set_solve_events(ds.handle, sv[k][0], sv[k][1])
+            api.orca_scene_set_bin_events(ds.handle, bv[k][0], bv[k][1])
             ev[k][0].record(stream)
             ds.step(1)
             ev[k][1].record(stream)
         barrier()
     api.orca_scene_set_solve_events(ds.handle, None, None)
+    api.orca_scene_set_bin_events(ds.handle, None, None)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     solve_ms = [api.event_elapsed_ms(a, b) for a, b in sv]
+    bin_ms = [api.event_elapsed_ms(a, b) for a, b in bv]
     total_s = sum(step_ms) / 1e3
     t = torch.tensor([total_s], device=dev)
     if world > 1:
@@ -426,6 +446,18 @@ def run_ours(args):
                 "counts_per_agent": {"candidates": c[0] / n, "neighbours": c[1] / n,
                                      "lp_pairs": c[2] / n, "fallback_frac": c[3] / n},
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz (nominal max clock)"}
+
+    # ---- binning phase (bin_count, 3-phase scan, scatter): HBM bound ----
+    ncells = int(ds.params.grid_nx) * int(ds.params.grid_ny)
+    bin_bytes = BIN_BYTES_AGENT * n + BIN_BYTES_CELL * ncells
+    bin_s = statistics.mean(bin_ms) / 1e3
+    hbm = float(_peaks().get("hbm_gbs", 6681.5))
+    roofline_binning = {"bound": "hbm", "achieved": bin_bytes / bin_s / 1e9, "peak": hbm,
+                        "unit": "GB/s", "frac": bin_bytes / bin_s / 1e9 / hbm, "traffic": None,
+                        "kernels": "bin_count + scan_blocks + scan_bsum + scan_add + scatter",
+                        "ms": statistics.mean(bin_ms), "bytes_per_step": bin_bytes,
+                        "cells": ncells, "launches_per_step": 5,
+                        "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)"}
 
     # ---- end to end through the public API from pinned host buffers ----
     e2e = None
@@ -466,9 +498,14 @@ def run_ours(args):
             "config": dict(cfg, l2="flushed before every timed step (256 MB write)",
                            parallelism=f"replicas{world}" if world > 1 else "single",
                            cell_size_m=float(ds.params.cell_size),
+                           solve_block=int(ds.params.block_size) or 128,
+                           autotune=None if tuned is None else
+                           [[a * float(scene.params.cell_size), bs, ms]
+                            for a, bs, ms in tuned.table],
                            neighbor_dist_m=10.0, max_neighbors=10, tau_s=5.0, dt_s=0.25),
             "clocks": clocks, "gpu_launches": ds.launch_count(1) * args.steps,
-            "roofline": roofline, "e2e": e2e, "status": status,
+            "roofline": roofline, "roofline_binning": roofline_binning, "e2e": e2e,
+            "status": status,
             "hbm_peak_gbs": peaks.get("hbm_gbs")}
     if not args.no_batched:
         line["batched"] = measure_batched(dev, flush)
@@ -495,6 +532,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -176,6 +176,13 @@ int orca_step(orca_scene *scene, int n_steps, const float *vpref_delta, void *st
 int orca_scene_set_solve_events(orca_scene *scene, void *begin, void *end);
 
 /*
+ * The same for the binning phase (cell keys, the scan of the cell counts and
+ * the scatter into cell order): begin is recorded before the bin_count
+ * kernel and end after the scatter kernel of every following step.
+ */
+int orca_scene_set_bin_events(orca_scene *scene, void *begin, void *end);
+
+/*
  * Work tallies for FLOP accounting, or NULL to stop.  counters is device
  * memory, uint64[5], accumulated (never cleared) by every following step:
  *   [0] candidate key tests of the neighbour search

@@ -92,6 +92,7 @@ SIGNATURES = {
                                ctypes.c_size_t, ctypes.POINTER(_V)]),
     "orca_scene_set_debug": (_I, [_V, _V, _V, _V, _V, _V]),
     "orca_scene_set_solve_events": (_I, [_V, _V, _V]),
+    "orca_scene_set_bin_events": (_I, [_V, _V, _V]),
     "orca_scene_set_counters": (_I, [_V, _V]),
     "orca_step": (_I, [_V, _I, _V, _V]),
     "orca_step_launch_count": (_I, [_V, _I]),

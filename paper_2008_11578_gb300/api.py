@@ -97,6 +97,17 @@ def orca_scene_set_solve_events(handle, begin=None, end=None):
     check(_lib.load().orca_scene_set_solve_events(handle, b, e), "orca_scene_set_solve_events")
 
 
+def orca_scene_set_bin_events(handle, begin=None, end=None):
+    """Bracket the binning phase (bin_count .. scatter) of every following
+    step with two torch CUDA events (or None to stop)."""
+    for ev in (begin, end):
+        if ev is not None and ev.cuda_event == 0:
+            ev.record()
+    b = None if begin is None else ctypes.c_void_p(begin.cuda_event)
+    e = None if end is None else ctypes.c_void_p(end.cuda_event)
+    check(_lib.load().orca_scene_set_bin_events(handle, b, e), "orca_scene_set_bin_events")
+
+
 def orca_scene_set_counters(handle, counters=None):
     """Accumulate work tallies into ``counters`` (int64[5] on the device)."""
     check(_lib.load().orca_scene_set_counters(handle, _ptr(counters)), "orca_scene_set_counters")

@@ -1,8 +1,10 @@
 // orca_capi.cu -- the C ABI of liborca (declared in include/orca.h).
 //
 // Host side of the ORCA step: argument validation, workspace layout, and
-// the launch sequence of one step (bin_count, scan x3, scatter, solve)
-// bracketed by a load and an unload kernel per call.
+// the launch sequence: per call a load kernel and the first step's bin_count,
+// then per step three scan kernels, the scatter and the solve kernel (which
+// bins the new positions for the next step, and writes the last step's
+// results straight into the caller's arrays).
 //
 // A single scene and a batch of independent scenes run the same kernels.  A
 // batch concatenates its scenes' agents (scene 0 first) and their grid cells
@@ -203,12 +205,10 @@ template <class SRC>
 void launch_solve(int mode, int grid, int block, size_t smem, cudaStream_t st, int n, SRC src,
                   const float2* pos, const float2* vel, const float* rad, const uint8_t* typ,
                   const int32_t* orig, const uint32_t* start, AgentIn ain, const float2* vpd,
-                  float2* out_pos, float2* out_vel, DebugOut dbg,
-                  unsigned long long* counters) {
-#define ORCA_SOLVE(M)                                                                   \
-    solve_kernel<SRC, M><<<grid, block, smem, st>>>(n, src, pos, vel, rad, typ, orig,    \
-                                                     start, ain, vpd, out_pos, out_vel, \
-                                                     dbg, counters)
+                  StepOut out, DebugOut dbg, unsigned long long* counters) {
+#define ORCA_SOLVE(M)                                                                \
+    solve_kernel<SRC, M><<<grid, block, smem, st>>>(n, src, pos, vel, rad, typ, orig, \
+                                                     start, ain, vpd, out, dbg, counters)
     if (mode == MODE_COUNT) ORCA_SOLVE(MODE_COUNT);
     else if (mode == MODE_RECORD) ORCA_SOLVE(MODE_RECORD);
     else ORCA_SOLVE(MODE_PLAIN);
@@ -233,6 +233,8 @@ struct Pipeline {
     DebugOut dbg;
     cudaEvent_t ev_begin;
     cudaEvent_t ev_end;
+    cudaEvent_t bin_begin;
+    cudaEvent_t bin_end;
     unsigned long long* counters;
     cudaGraphExec_t graph;
     int graph_steps;
@@ -251,7 +253,7 @@ int step_mode(const Pipeline& P) {
     return P.dbg.act != nullptr ? MODE_RECORD : MODE_PLAIN;
 }
 
-// Enqueue load, n_steps steps and unload.  dbg_for(t) gives the solve
+// Enqueue the load and n_steps steps.  dbg_for(t) gives the solve
 // kernel's optional outputs of step t.
 template <class SRC, class DBG>
 void enqueue_steps(const Pipeline& P, SRC src, int n_steps, const float* vpref_delta,
@@ -275,7 +277,9 @@ void enqueue_steps(const Pipeline& P, SRC src, int n_steps, const float* vpref_d
     const int sgrid = (n + sb - 1) / sb;
     const size_t smem = solve_smem(P);
     for (int t = 0; t < n_steps; ++t) {
-        bin_count_kernel<SRC><<<gb, tb, 0, st>>>(n, src, B.pos0, B.key, B.slot, B.count);
+        if (P.bin_begin) cudaEventRecord(P.bin_begin, st);
+        // later steps were binned by the previous step's solve kernel
+        if (t == 0) bin_count_kernel<SRC><<<gb, tb, 0, st>>>(n, src, B.pos0, B.key, B.slot, B.count);
         scan_blocks_kernel<<<P.nblocks, kScanThreads, 0, st>>>(B.count, B.start, B.bsum,
                                                                P.ncells);
         scan_bsum_kernel<<<1, 1024, 0, st>>>(B.bsum, P.nblocks);
@@ -285,16 +289,18 @@ void enqueue_steps(const Pipeline& P, SRC src, int n_steps, const float* vpref_d
                                           B.rad[cur], B.typ[cur], B.orig[cur], B.pos1, B.vel1,
                                           B.rad[1 - cur], B.typ[1 - cur], B.orig[1 - cur]);
         cur = 1 - cur;
+        if (P.bin_end) cudaEventRecord(P.bin_end, st);
         const float2* vpd =
             vpref_delta ? (const float2*)vpref_delta + (size_t)t * (size_t)n : nullptr;
         if (P.ev_begin) cudaEventRecord(P.ev_begin, st);
+        const bool last = t == n_steps - 1;
+        const StepOut out = last ? StepOut{(float2*)A.pos, (float2*)A.vel, true, nullptr, nullptr,
+                                           nullptr}
+                                 : StepOut{B.pos0, B.vel0, false, B.key, B.slot, B.count};
         launch_solve(mode, sgrid, sb, smem, st, n, src, B.pos1, B.vel1, B.rad[cur],
-                     B.typ[cur], B.orig[cur], B.start, ain, vpd, B.pos0, B.vel0, dbg_for(t),
-                     P.counters);
+                     B.typ[cur], B.orig[cur], B.start, ain, vpd, out, dbg_for(t), P.counters);
         if (P.ev_end) cudaEventRecord(P.ev_end, st);
     }
-    unload_kernel<<<gb, tb, 0, st>>>(n, B.orig[cur], B.pos0, B.vel0, (float2*)A.pos,
-                                     (float2*)A.vel);
 }
 
 int run_steps(const Pipeline& P, int n_steps, const float* vpref_delta, cudaStream_t st) {
@@ -327,7 +333,7 @@ int read_status(const Pipeline& P) {
 int launch_count(const Pipeline& P, int n_steps) {
     if (n_steps < 0) return -1;
     if (P.n == 0 || n_steps == 0) return 0;
-    return 2 + 6 * n_steps;
+    return 2 + 5 * n_steps;   // load + bin_count, then 3 scans + scatter + solve per step
 }
 
 void drop_graph(Pipeline& P) {
@@ -347,9 +353,9 @@ int capture_graph(Pipeline& P, int n_steps, const float* vpref_delta) {
     if (st != ORCA_OK) return st;
     cudaStream_t cs = nullptr;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return ORCA_ERR_CUDA;
-    cudaEvent_t eb = P.ev_begin, ee = P.ev_end;
+    cudaEvent_t eb = P.ev_begin, ee = P.ev_end, bb = P.bin_begin, be = P.bin_end;
     unsigned long long* cn = P.counters;
-    P.ev_begin = P.ev_end = nullptr;
+    P.ev_begin = P.ev_end = P.bin_begin = P.bin_end = nullptr;
     P.counters = nullptr;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
@@ -360,6 +366,8 @@ int capture_graph(Pipeline& P, int n_steps, const float* vpref_delta) {
     }
     P.ev_begin = eb;
     P.ev_end = ee;
+    P.bin_begin = bb;
+    P.bin_end = be;
     P.counters = cn;
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
@@ -394,6 +402,7 @@ void init_pipeline(Pipeline& P, const orca_agents* agents, int ncells, int kcap,
     P.dbg = DebugOut{};
     P.dbg.k_stride = k_stride;
     P.ev_begin = P.ev_end = nullptr;
+    P.bin_begin = P.bin_end = nullptr;
     P.counters = nullptr;
     P.graph = nullptr;
     P.graph_steps = 0;
@@ -618,6 +627,13 @@ int orca_scene_set_solve_events(orca_scene* s, void* begin, void* end) {
     return ORCA_OK;
 }
 
+int orca_scene_set_bin_events(orca_scene* s, void* begin, void* end) {
+    if (!s || ((begin == nullptr) != (end == nullptr))) return ORCA_ERR_INVALID_ARG;
+    s->p.bin_begin = (cudaEvent_t)begin;
+    s->p.bin_end = (cudaEvent_t)end;
+    return ORCA_OK;
+}
+
 int orca_scene_set_counters(orca_scene* s, unsigned long long* counters) {
     if (!s || (counters && !aligned(counters, 8))) return ORCA_ERR_INVALID_ARG;
     s->p.counters = counters;
@@ -747,7 +763,7 @@ int orca_adjoint(orca_scene* s, int n_steps, int ckpt_every, const float* vpref_
     R.agents.pos = (float*)(w + L.rp_pos);
     R.agents.vel = (float*)(w + L.rp_vel);
     if (A.route) R.agents.wp_idx = (uint8_t*)(w + L.rp_wp);
-    R.ev_begin = R.ev_end = nullptr;
+    R.ev_begin = R.ev_end = R.bin_begin = R.bin_end = nullptr;
     R.counters = nullptr;
     R.graph = nullptr;
     ReplayDebug rec{DebugOut{}, (float2*)(w + L.r_pos), (float2*)(w + L.r_vel),
@@ -825,7 +841,7 @@ int orca_step_vjp(orca_scene* s, void* adj_ws, size_t adj_bytes, const float* po
     R.agents.pos = (float*)(w + L.rp_pos);
     R.agents.vel = (float*)(w + L.rp_vel);
     if (A.route) R.agents.wp_idx = (uint8_t*)(w + L.rp_wp);
-    R.ev_begin = R.ev_end = nullptr;
+    R.ev_begin = R.ev_end = R.bin_begin = R.bin_end = nullptr;
     R.counters = nullptr;
     R.graph = nullptr;
     bool ok = cudaMemcpyAsync(R.agents.pos, pos, nb, cudaMemcpyDeviceToDevice, stm) ==
@@ -865,7 +881,7 @@ int orca_adjoint_launch_count(const orca_scene* s, int n_steps, int ckpt_every) 
     if (!s || n_steps < 0 || ckpt_every < 1) return -1;
     if (s->p.n == 0 || n_steps == 0) return 0;
     const int n_ck = (n_steps + ckpt_every - 1) / ckpt_every;
-    return n_ck * 2 + 6 * n_steps + n_steps;   // replays (load/unload + steps) + adjoint kernels
+    return n_ck * 2 + 5 * n_steps + n_steps;   // replays (load + bin_count + steps) + adjoint kernels
 }
 
 // ------------------------------------------------------------- batches ----

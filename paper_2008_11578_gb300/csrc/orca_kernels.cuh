@@ -7,10 +7,12 @@
 //                    the load kernel)
 //   sorted order     pos1/vel1 + rad/typ/orig: agents grouped by grid cell,
 //                    cells in row-major order, scenes one after another
-// One step: bin_count (key + per-cell slot) -> 3-phase exclusive scan of the
-// cell counts -> scatter into sorted order -> solve (one thread per agent:
+// One step: cell keys and per-cell slots (bin_count for a call's first step,
+// the previous solve afterwards) -> 3-phase exclusive scan of the cell
+// counts -> scatter into sorted order -> solve (one thread per agent:
 // k-nearest ring search, ORCA lines, LP, integrate) writing pos0/vel0 in
-// sorted order, which becomes the state order of the next step.
+// sorted order, which becomes the state order of the next step; the last
+// step of a call writes the caller's arrays instead.
 #pragma once
 
 #include <climits>
@@ -54,6 +56,21 @@ struct AgentIn {
     const float2* __restrict__ waypoints;
     int n_waypoints;
     uint8_t* __restrict__ wp_idx;          // may be null when route is null
+};
+
+// Where the solve kernel writes the new state.  Ordinary steps write pos/vel
+// in sorted order (the next step's state order) and, when key is set, the
+// next step's cell key and counter slot, which saves that step's bin_count
+// launch.  The last step of a call writes straight to the caller's arrays at
+// the original index instead (caller_order), so no separate kernel has to
+// copy the results back to the caller's order.
+struct StepOut {
+    float2* pos;
+    float2* vel;
+    bool caller_order;
+    uint32_t* key;
+    uint32_t* slot;
+    uint32_t* count;
 };
 
 // Optional per-agent outputs of the solve kernel, caller order, any of them

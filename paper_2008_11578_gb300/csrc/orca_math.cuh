@@ -180,7 +180,9 @@ __host__ __device__ __forceinline__ bool act_overlap(uint32_t a, int m) {
 
 // ---------------------------------------------------------------------------
 // Velocity LP (paper Sec. 3, LP paragraphs).  Lines live in shared memory at
-// L[i * stride].  The objective is the Euclidean distance to v_pref, so the
+// L[i * stride].  Interval bounds divide by determinants of unit directions
+// (|den| <= 2), so the fast 2-ulp division is safe and costs two
+// instructions instead of the IEEE sequence.  The objective is the Euclidean distance to v_pref, so the
 // incremental scheme is exact: when the current optimum violates line i, the
 // new optimum lies on line i, and a 1D problem on that line with the earlier
 // lines and the speed disc finds it.
@@ -209,7 +211,7 @@ __device__ __forceinline__ bool lp1_project(const float4* __restrict__ L, int st
             if (num < 0.0f) return false;
             continue;
         }
-        float t = num / den;
+        float t = __fdividef(num, den);
         if (den > 0.0f) {
             if (t < tr) jr = j;
             tr = fminf(tr, t);
@@ -273,7 +275,7 @@ __device__ __forceinline__ bool bisector(float4 li, float4 lj, float4& b) {
     if (a2 <= 1e-12f) return false;
     const float ci = li.z * li.y - li.w * li.x;
     const float cj = lj.z * lj.y - lj.w * lj.x;
-    const float s = (cj - ci) / a2;
+    const float s = __fdividef(cj - ci, a2);
     const float inv = rsqrtf(a2);
     b = make_float4(ax * s, ay * s, ay * inv, -ax * inv);
     return true;
@@ -331,7 +333,7 @@ __device__ __forceinline__ float lp3_min_penetration(const float4* __restrict__ 
                     if (num > 0.0f) { ok = false; break; }
                     continue;
                 }
-                const float tt = num / den;
+                const float tt = __fdividef(num, den);
                 if (den < 0.0f) {
                     if (tt < tr) kr = jj;
                     tr = fminf(tr, tt);
@@ -406,7 +408,7 @@ __device__ __forceinline__ bool valley_tie_break(const float4* __restrict__ L, i
             if (num < 0.0f) return false;
             continue;
         }
-        const float s = num / den;
+        const float s = __fdividef(num, den);
         if (den > 0.0f) {
             if (s < tr) kr = k;
             tr = fminf(tr, s);

@@ -1,6 +1,6 @@
 // orca_step_kernels.cuh -- device kernels of the ORCA step (sm_103a).
 //
-// Memory-bound kernels (load, bin_count, scan, scatter, unload) are one
+// Memory-bound kernels (load, bin_count, scan, scatter) are one
 // thread per element with coalesced accesses; the solve kernel is one thread
 // per agent in cell-sorted order, so the 32 agents of a warp come from a few
 // neighbouring cells and read the same candidate cells through L1.
@@ -159,17 +159,6 @@ __global__ void scatter_kernel(int n, const uint32_t* __restrict__ key,
     orig_b[s] = orig_a[i];
 }
 
-// ---------------------------------------------------------------- unload ----
-__global__ void unload_kernel(int n, const int32_t* __restrict__ orig,
-                              const float2* __restrict__ pos0, const float2* __restrict__ vel0,
-                              float2* __restrict__ upos, float2* __restrict__ uvel) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    int o = orig[s];
-    upos[o] = pos0[s];
-    uvel[o] = vel0[s];
-}
-
 // ----------------------------------------------------------------- solve ----
 // One thread per agent (sorted slot s).  The neighbour list and then the
 // lines are kept in dynamic shared memory (k float4 slots per thread), slot i
@@ -181,8 +170,7 @@ __global__ void __launch_bounds__(128)
 solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __restrict__ vel,
              const float* __restrict__ rad, const uint8_t* __restrict__ typ,
              const int32_t* __restrict__ orig, const uint32_t* __restrict__ cstart,
-             AgentIn ain, const float2* __restrict__ vpd, float2* __restrict__ out_pos,
-             float2* __restrict__ out_vel, DebugOut dbg,
+             AgentIn ain, const float2* __restrict__ vpd, StepOut out, DebugOut dbg,
              unsigned long long* __restrict__ counters) {
     extern __shared__ float4 smem_lines[];
     const int stride = blockDim.x;
@@ -341,9 +329,19 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     const uint8_t flags = (uint8_t)(infeasible | (any_overlap ? 4 : 0));
 
     // ---- integrate ----
-    out_vel[s] = make_float2(vx, vy);
-    out_pos[s] = make_float2(__fadd_rn(p.x, __fmul_rn(sc.dt, vx)),
-                             __fadd_rn(p.y, __fmul_rn(sc.dt, vy)));
+    const float2 pn = make_float2(__fadd_rn(p.x, __fmul_rn(sc.dt, vx)),
+                                  __fadd_rn(p.y, __fmul_rn(sc.dt, vy)));
+    const int w = out.caller_order ? o : s;
+    out.vel[w] = make_float2(vx, vy);
+    out.pos[w] = pn;
+    if (out.key != nullptr) {
+        // bin the new position for the next step (as bin_count_kernel does)
+        const int ncx = cell_axis(pn.x, sc.origin_x, sc.inv_cell, sc.nx);
+        const int ncy = cell_axis(pn.y, sc.origin_y, sc.inv_cell, sc.ny);
+        const uint32_t c = (uint32_t)(sc.cell_off + ncy * sc.nx + ncx);
+        out.key[s] = c;
+        out.slot[s] = atomicAdd(out.count + c, 1u);
+    }
 
     if (dbg.spos != nullptr) dbg.spos[o] = p;
     if (dbg.svel != nullptr) dbg.svel[o] = v;
