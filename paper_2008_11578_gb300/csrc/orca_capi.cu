@@ -36,7 +36,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // id of every slot exist only for batches (n_scenes > 0).
 struct Layout {
     size_t err, count, start, bsum, key, slot, pos0, vel0, pos1, vel1;
-    size_t rad[2], typ[2], orig[2];
+    size_t aux[2];
     size_t scenes, sid;
     size_t total;
 };
@@ -61,9 +61,7 @@ Layout make_layout(size_t n, size_t ncells, size_t n_scenes) {
     L.pos1 = take(n * 8);
     L.vel1 = take(n * 8);
     for (int b = 0; b < 2; ++b) {
-        L.rad[b] = take(n * 4);
-        L.typ[b] = take(n);
-        L.orig[b] = take(n * 4);
+        L.aux[b] = take(n * 8);
     }
     if (n_scenes > 0) {
         L.scenes = take(n_scenes * sizeof(SceneDev));
@@ -78,9 +76,7 @@ struct Buffers {
     int* err;
     uint32_t *count, *start, *bsum, *key, *slot;
     float2 *pos0, *vel0, *pos1, *vel1;
-    float* rad[2];
-    uint8_t* typ[2];
-    int32_t* orig[2];
+    uint2* aux[2];
     SceneDev* scenes;
     int32_t* sid;
 };
@@ -98,9 +94,7 @@ Buffers carve(char* w, const Layout& L, bool batch) {
     b.pos1 = (float2*)(w + L.pos1);
     b.vel1 = (float2*)(w + L.vel1);
     for (int i = 0; i < 2; ++i) {
-        b.rad[i] = (float*)(w + L.rad[i]);
-        b.typ[i] = (uint8_t*)(w + L.typ[i]);
-        b.orig[i] = (int32_t*)(w + L.orig[i]);
+        b.aux[i] = (uint2*)(w + L.aux[i]);
     }
     b.scenes = batch ? (SceneDev*)(w + L.scenes) : nullptr;
     b.sid = batch ? (int32_t*)(w + L.sid) : nullptr;
@@ -203,12 +197,12 @@ cudaError_t prepare_solve(size_t smem) {
 
 template <class SRC>
 void launch_solve(int mode, int grid, int block, size_t smem, cudaStream_t st, int n, SRC src,
-                  const float2* pos, const float2* vel, const float* rad, const uint8_t* typ,
-                  const int32_t* orig, const uint32_t* start, AgentIn ain, const float2* vpd,
-                  StepOut out, DebugOut dbg, unsigned long long* counters) {
-#define ORCA_SOLVE(M)                                                                \
-    solve_kernel<SRC, M><<<grid, block, smem, st>>>(n, src, pos, vel, rad, typ, orig, \
-                                                     start, ain, vpd, out, dbg, counters)
+                  const float2* pos, const float2* vel, const uint2* aux, const uint32_t* start,
+                  AgentIn ain, const float2* vpd, StepOut out, DebugOut dbg,
+                  unsigned long long* counters) {
+#define ORCA_SOLVE(M)                                                                    \
+    solve_kernel<SRC, M><<<grid, block, smem, st>>>(n, src, pos, vel, aux, start, ain, vpd, \
+                                                     out, dbg, counters)
     if (mode == MODE_COUNT) ORCA_SOLVE(MODE_COUNT);
     else if (mode == MODE_RECORD) ORCA_SOLVE(MODE_RECORD);
     else ORCA_SOLVE(MODE_PLAIN);
@@ -267,8 +261,8 @@ void enqueue_steps(const Pipeline& P, SRC src, int n_steps, const float* vpref_d
         int g = (std::max(n, P.ncells) + tb - 1) / tb;
         g = std::min(g, 152 * 16);
         load_kernel<<<g, tb, 0, st>>>(n, (const float2*)A.pos, (const float2*)A.vel, A.radius,
-                                      A.type, B.pos0, B.vel0, B.rad[0], B.typ[0], B.orig[0],
-                                      B.count, P.ncells, B.err);
+                                      A.type, B.pos0, B.vel0, B.aux[0], B.count, P.ncells,
+                                      B.err);
     }
     AgentIn ain{(const float2*)A.goal, A.max_speed, A.route, (const float2*)A.waypoints,
                 A.n_waypoints, A.wp_idx};
@@ -283,11 +277,10 @@ void enqueue_steps(const Pipeline& P, SRC src, int n_steps, const float* vpref_d
         scan_blocks_kernel<<<P.nblocks, kScanThreads, 0, st>>>(B.count, B.start, B.bsum,
                                                                P.ncells);
         scan_bsum_kernel<<<1, 1024, 0, st>>>(B.bsum, P.nblocks);
-        scan_add_kernel<<<(P.ncells + 255) / 256, 256, 0, st>>>(B.start, B.bsum, P.ncells,
-                                                                P.nblocks);
+        scan_add_kernel<<<(P.ncells / 4 + 256) / 256, 256, 0, st>>>(B.start, B.bsum, P.ncells,
+                                                                    P.nblocks);
         scatter_kernel<<<gb, tb, 0, st>>>(n, B.key, B.slot, B.start, B.pos0, B.vel0,
-                                          B.rad[cur], B.typ[cur], B.orig[cur], B.pos1, B.vel1,
-                                          B.rad[1 - cur], B.typ[1 - cur], B.orig[1 - cur]);
+                                          B.aux[cur], B.pos1, B.vel1, B.aux[1 - cur]);
         cur = 1 - cur;
         if (P.bin_end) cudaEventRecord(P.bin_end, st);
         const float2* vpd =
@@ -297,8 +290,8 @@ void enqueue_steps(const Pipeline& P, SRC src, int n_steps, const float* vpref_d
         const StepOut out = last ? StepOut{(float2*)A.pos, (float2*)A.vel, true, nullptr, nullptr,
                                            nullptr}
                                  : StepOut{B.pos0, B.vel0, false, B.key, B.slot, B.count};
-        launch_solve(mode, sgrid, sb, smem, st, n, src, B.pos1, B.vel1, B.rad[cur],
-                     B.typ[cur], B.orig[cur], B.start, ain, vpd, out, dbg_for(t), P.counters);
+        launch_solve(mode, sgrid, sb, smem, st, n, src, B.pos1, B.vel1, B.aux[cur], B.start,
+                     ain, vpd, out, dbg_for(t), P.counters);
         if (P.ev_end) cudaEventRecord(P.ev_end, st);
     }
 }

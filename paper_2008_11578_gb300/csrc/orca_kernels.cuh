@@ -5,7 +5,8 @@
 //   "state" order    pos0/vel0: output of the solve kernel, in the cell order
 //                    of the step that produced it (caller order right after
 //                    the load kernel)
-//   sorted order     pos1/vel1 + rad/typ/orig: agents grouped by grid cell,
+//   sorted order     pos1/vel1 + aux (radius, type, original index): agents
+//                    grouped by grid cell,
 //                    cells in row-major order, scenes one after another
 // One step: cell keys and per-cell slots (bin_count for a call's first step,
 // the previous solve afterwards) -> 3-phase exclusive scan of the cell
@@ -57,6 +58,18 @@ struct AgentIn {
     int n_waypoints;
     uint8_t* __restrict__ wp_idx;          // may be null when route is null
 };
+
+// Per-agent constants of the sorted state, packed in 8 bytes so that the
+// scatter moves one word for them: the radius, and the original index with
+// the agent type (0 pedestrian, 1 vehicle) in its top bit.
+__host__ __device__ __forceinline__ uint2 aux_pack(float r, int type, int orig) {
+    union { float f; uint32_t u; } c;
+    c.f = r;
+    return make_uint2(c.u, (uint32_t)orig | (type ? 0x80000000u : 0u));
+}
+__device__ __forceinline__ float aux_rad(uint2 a) { return __uint_as_float(a.x); }
+__device__ __forceinline__ int aux_orig(uint2 a) { return (int)(a.y & 0x7fffffffu); }
+__device__ __forceinline__ int aux_type(uint2 a) { return (int)(a.y >> 31); }
 
 // Where the solve kernel writes the new state.  Ordinary steps write pos/vel
 // in sorted order (the next step's state order) and, when key is set, the

@@ -15,8 +15,7 @@ __global__ void load_kernel(int n, const float2* __restrict__ upos,
                             const float2* __restrict__ uvel,
                             const float* __restrict__ uradius,
                             const uint8_t* __restrict__ utype, float2* __restrict__ pos0,
-                            float2* __restrict__ vel0, float* __restrict__ rad,
-                            uint8_t* __restrict__ typ, int32_t* __restrict__ orig,
+                            float2* __restrict__ vel0, uint2* __restrict__ aux,
                             uint32_t* __restrict__ count, int ncells, int* __restrict__ err) {
     int stride = gridDim.x * blockDim.x;
     int i0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -27,9 +26,7 @@ __global__ void load_kernel(int n, const float2* __restrict__ upos,
         bad |= !(isfinite(p.x) && isfinite(p.y) && isfinite(v.x) && isfinite(v.y));
         pos0[i] = p;
         vel0[i] = v;
-        rad[i] = uradius[i];
-        typ[i] = utype[i];
-        orig[i] = i;
+        aux[i] = aux_pack(uradius[i], utype[i], i);
     }
     if (bad) atomicOr(err, ERR_BIT_NONFINITE);
 }
@@ -87,27 +84,50 @@ __global__ void __launch_bounds__(kScanThreads)
 scan_blocks_kernel(uint32_t* __restrict__ count, uint32_t* __restrict__ start,
                    uint32_t* __restrict__ bsum, int ncells) {
     __shared__ uint32_t ws[32];
-    int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+    static_assert(kScanItems == 16, "four 16-byte vectors per thread");
+    const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
     uint32_t s = 0;
+    const bool whole = base + kScanItems <= ncells;   // 64-byte aligned full chunk
+    if (whole) {
+        uint4* c4 = reinterpret_cast<uint4*>(count + base);
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        int c = base + j;
-        v[j] = c < ncells ? count[c] : 0u;
-        s += v[j];
+        for (int q = 0; q < 4; ++q) {
+            const uint4 x = c4[q];
+            v[4 * q] = x.x;
+            v[4 * q + 1] = x.y;
+            v[4 * q + 2] = x.z;
+            v[4 * q + 3] = x.w;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) c4[q] = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            const int c = base + j;
+            v[j] = c < ncells ? count[c] : 0u;
+            if (c < ncells) count[c] = 0u;
+        }
     }
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        int c = base + j;
-        if (c < ncells) count[c] = 0u;
-    }
+    for (int j = 0; j < kScanItems; ++j) s += v[j];
     uint32_t total;
     uint32_t pre = block_excl_scan(s, ws, total);
+    uint32_t o[kScanItems];
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        int c = base + j;
-        if (c < ncells) start[c] = pre;
+        o[j] = pre;
         pre += v[j];
+    }
+    if (whole) {
+        uint4* s4 = reinterpret_cast<uint4*>(start + base);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            s4[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j)
+            if (base + j < ncells) start[base + j] = o[j];
     }
     if (threadIdx.x == 0) bsum[blockIdx.x] = total;
 }
@@ -133,10 +153,23 @@ __global__ void __launch_bounds__(1024) scan_bsum_kernel(uint32_t* __restrict__ 
     if (threadIdx.x == 0) bsum[nb] = total;
 }
 
+// one thread per four cells (16-byte aligned vectors; kScanChunk is a
+// multiple of 4, so the four share one block offset)
 __global__ void scan_add_kernel(uint32_t* __restrict__ start, const uint32_t* __restrict__ bsum,
                                 int ncells, int nb) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < ncells) start[c] += bsum[c / kScanChunk];
+    const int c = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (c + 4 <= ncells) {
+        const uint32_t b = bsum[c / kScanChunk];
+        uint4* s4 = reinterpret_cast<uint4*>(start + c);
+        uint4 x = *s4;
+        x.x += b;
+        x.y += b;
+        x.z += b;
+        x.w += b;
+        *s4 = x;
+    } else {
+        for (int q = c; q < ncells && q < c + 4; ++q) start[q] += bsum[q / kScanChunk];
+    }
     if (c == 0) start[ncells] = bsum[nb];
 }
 
@@ -145,18 +178,14 @@ __global__ void scatter_kernel(int n, const uint32_t* __restrict__ key,
                                const uint32_t* __restrict__ slot,
                                const uint32_t* __restrict__ start,
                                const float2* __restrict__ pos0, const float2* __restrict__ vel0,
-                               const float* __restrict__ rad_a, const uint8_t* __restrict__ typ_a,
-                               const int32_t* __restrict__ orig_a, float2* __restrict__ pos1,
-                               float2* __restrict__ vel1, float* __restrict__ rad_b,
-                               uint8_t* __restrict__ typ_b, int32_t* __restrict__ orig_b) {
+                               const uint2* __restrict__ aux_a, float2* __restrict__ pos1,
+                               float2* __restrict__ vel1, uint2* __restrict__ aux_b) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t s = start[key[i]] + slot[i];
     pos1[s] = pos0[i];
     vel1[s] = vel0[i];
-    rad_b[s] = rad_a[i];
-    typ_b[s] = typ_a[i];
-    orig_b[s] = orig_a[i];
+    aux_b[s] = aux_a[i];
 }
 
 // ----------------------------------------------------------------- solve ----
@@ -168,8 +197,7 @@ __global__ void scatter_kernel(int n, const uint32_t* __restrict__ key,
 template <class SRC, int MODE>
 __global__ void __launch_bounds__(128)
 solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __restrict__ vel,
-             const float* __restrict__ rad, const uint8_t* __restrict__ typ,
-             const int32_t* __restrict__ orig, const uint32_t* __restrict__ cstart,
+             const uint2* __restrict__ aux, const uint32_t* __restrict__ cstart,
              AgentIn ain, const float2* __restrict__ vpd, StepOut out, DebugOut dbg,
              unsigned long long* __restrict__ counters) {
     extern __shared__ float4 smem_lines[];
@@ -180,9 +208,10 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     const SceneDev sc = src.get(s);
     const float2 p = pos[s];
     const float2 v = vel[s];
-    const float r = rad[s];
-    const int ta = typ[s];
-    const int o = orig[s];
+    const uint2 as = aux[s];
+    const float r = aux_rad(as);
+    const int ta = aux_type(as);
+    const int o = aux_orig(as);
     const int cx = cell_axis(p.x, sc.origin_x, sc.inv_cell, sc.nx);
     const int cy = cell_axis(p.y, sc.origin_y, sc.inv_cell, sc.ny);
 
@@ -228,7 +257,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                     const float2 q = pos[j];
                     const float d2 = key_d2(p.x, p.y, q.x, q.y);
                     if (d2 < R2 && d2 <= thr_d && j != s) {
-                        const int oj = __ldg(orig + j);
+                        const int oj = aux_orig(__ldg(aux + j));
                         if (d2 < thr_d || oj < thr_o) {
                             int at = min(cnt, k - 1);   // a full list drops its last entry
                             while (at > 0) {
@@ -306,8 +335,9 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         const float4 e = L[i * stride];
         const int j = __float_as_int(e.y);
         const float2 pj = pos[j], vj = vel[j];
-        const float rj = rad[j];
-        const int tb = typ[j];
+        const uint2 aj = aux[j];
+        const float rj = aux_rad(aj);
+        const int tb = aux_type(aj);
         const float rs = __fadd_rn(r, rj);
         const bool ov = e.x <= __fmul_rn(rs, rs);
         any_overlap |= ov;
