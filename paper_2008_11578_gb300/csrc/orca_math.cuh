@@ -188,6 +188,13 @@ __host__ __device__ __forceinline__ bool act_overlap(uint32_t a, int m) {
 // lines and the speed disc finds it.
 // ---------------------------------------------------------------------------
 
+// Rounding allowance of the LP's emptiness tests, in m/s.  Intervals whose
+// ends cross by less than this are rounding, not infeasibility: half-planes
+// of f = 0 pairs all pass through the agent's own velocity, and when that
+// lies on the speed circle their exact common point meets the circle's
+// rounded end (a vehicle at full speed among pedestrians).
+__device__ __forceinline__ float lp_tol(float vmax) { return 1e-5f * (1.0f + vmax); }
+
 // 1D problem on line i: the point of line i closest to v_pref that keeps
 // lines 0..i-1 and the disc.  Returns false when that set is empty.
 // bound: the constraint that binds the result on line i (-2 none, -1 the
@@ -196,10 +203,11 @@ __device__ __forceinline__ bool lp1_project(const float4* __restrict__ L, int st
                                             float vmax, float vpx, float vpy, float& ox,
                                             float& oy, int& work, int& bound) {
     float4 li = L[i * stride];
+    const float tol = lp_tol(vmax);
     float dot = li.x * li.z + li.y * li.w;
     float disc = dot * dot + vmax * vmax - (li.x * li.x + li.y * li.y);
-    if (disc < 0.0f) return false;
-    float sq = sqrtf(disc);
+    if (disc < -tol * (1.0f + vmax)) return false;
+    float sq = sqrtf(fmaxf(disc, 0.0f));
     float tl = -dot - sq, tr = -dot + sq;
     int jl = -1, jr = -1;
     for (int j = 0; j < i; ++j) {
@@ -208,7 +216,7 @@ __device__ __forceinline__ bool lp1_project(const float4* __restrict__ L, int st
         float den = li.z * lj.w - li.w * lj.z;                     // det(d_i, d_j)
         float num = lj.z * (li.y - lj.y) - lj.w * (li.x - lj.x);   // det(d_j, P_i - P_j)
         if (den == 0.0f) {
-            if (num < 0.0f) return false;
+            if (num < -tol) return false;
             continue;
         }
         float t = __fdividef(num, den);
@@ -219,7 +227,7 @@ __device__ __forceinline__ bool lp1_project(const float4* __restrict__ L, int st
             if (t > tl) jl = j;
             tl = fmaxf(tl, t);
         }
-        if (tl > tr) return false;
+        if (tl > tr + tol) return false;
     }
     float t0 = li.z * (vpx - li.x) + li.w * (vpy - li.y);
     float t = fminf(fmaxf(t0, tl), tr);
@@ -289,6 +297,7 @@ __device__ __forceinline__ bool bisector(float4 li, float4 lj, float4& b) {
 __device__ __forceinline__ float lp3_min_penetration(const float4* __restrict__ L, int stride,
                                                      int n, float vmax, float& vx, float& vy,
                                                      int& work, uint32_t& act) {
+    const float tol = lp_tol(vmax);
     float4 l0 = L[0];
     vx = -l0.w * vmax;
     vy = l0.z * vmax;
@@ -314,8 +323,8 @@ __device__ __forceinline__ float lp3_min_penetration(const float4* __restrict__ 
             if (!bisector(li, lj, bj)) continue;
             float dot = bj.x * bj.z + bj.y * bj.w;
             float disc = dot * dot + vmax * vmax - (bj.x * bj.x + bj.y * bj.y);
-            if (disc < 0.0f) continue;
-            float sq = sqrtf(disc);
+            if (disc < -tol * (1.0f + vmax)) continue;
+            float sq = sqrtf(fmaxf(disc, 0.0f));
             float tl = -dot - sq, tr = -dot + sq;
             int kl = -1, kr = -1;
             bool ok = true;
@@ -330,7 +339,7 @@ __device__ __forceinline__ float lp3_min_penetration(const float4* __restrict__ 
                 const float den = ax * bj.z + ay * bj.w;
                 const float num = beta - (ax * bj.x + ay * bj.y);
                 if (den == 0.0f) {
-                    if (num > 0.0f) { ok = false; break; }
+                    if (num > tol) { ok = false; break; }
                     continue;
                 }
                 const float tt = __fdividef(num, den);
@@ -341,7 +350,7 @@ __device__ __forceinline__ float lp3_min_penetration(const float4* __restrict__ 
                     if (tt > tl) kl = jj;
                     tl = fmaxf(tl, tt);
                 }
-                if (tl > tr) { ok = false; break; }
+                if (tl > tr + tol) { ok = false; break; }
             }
             if (!ok) continue;   // empty only through rounding: keep the point
             const bool right = nix * bj.z + niy * bj.w > 0.0f;
@@ -390,10 +399,11 @@ __device__ __forceinline__ bool valley_tie_break(const float4* __restrict__ L, i
     if (vi < 0) return false;
     float4 m;
     if (!bisector(L[vi * stride], L[vj * stride], m)) return false;
+    const float tol = lp_tol(vmax);
     const float dot = m.x * m.z + m.y * m.w;
     const float disc = dot * dot + vmax * vmax - (m.x * m.x + m.y * m.y);
-    if (disc < 0.0f) return false;
-    const float sq = sqrtf(disc);
+    if (disc < -tol * (1.0f + vmax)) return false;
+    const float sq = sqrtf(fmaxf(disc, 0.0f));
     float tl = -dot - sq, tr = -dot + sq;
     const float T = t3 + 1e-6f * (1.0f + fabsf(t3));
     int kl = -1, kr = -1;
@@ -405,7 +415,7 @@ __device__ __forceinline__ bool valley_tie_break(const float4* __restrict__ L, i
         const float den = m.z * lk.w - m.w * lk.z;
         const float num = T - (lk.z * (lk.y - m.y) - lk.w * (lk.x - m.x));
         if (den == 0.0f) {
-            if (num < 0.0f) return false;
+            if (num < -tol) return false;
             continue;
         }
         const float s = __fdividef(num, den);
@@ -417,7 +427,7 @@ __device__ __forceinline__ bool valley_tie_break(const float4* __restrict__ L, i
             tl = fmaxf(tl, s);
         }
     }
-    if (tl > tr) return false;
+    if (tl > tr + tol) return false;
     const float s0 = m.z * (vpx - m.x) + m.w * (vpy - m.y);
     const float s = fminf(fmaxf(s0, tl), tr);
     const int kb = (s0 > tr) ? kr : ((s0 < tl) ? kl : -2);

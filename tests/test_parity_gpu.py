@@ -172,3 +172,49 @@ def test_launch_count():
     assert ds.launch_count(3) == 2 + 5 * 3
     assert ds.launch_count(0) == 0
     ds.close()
+
+
+def _full_speed_vehicle_apexes(count=24, seed=60):
+    """Small groups, each a vehicle moving at exactly its maximum speed among
+    pedestrians, kept only where the oracle's answer is the vehicle's own
+    velocity: the apex of its f = 0 half-planes (car|person), which all pass
+    through that velocity and here lie on the speed circle.  Groups sit 100 m
+    apart, so they do not interact."""
+    rng = np.random.default_rng(seed)
+    groups = []
+    while len(groups) < count:
+        th = rng.uniform(0, 2 * np.pi)
+        v0 = np.array([5.0 * np.cos(th), 5.0 * np.sin(th)], np.float32)
+        if float(v0[0]) ** 2 + float(v0[1]) ** 2 <= 25.0:
+            continue        # keep headings whose FP32 velocity is a hair outside the circle,
+                            # as an earlier step's clip to max speed leaves it
+        m = int(rng.integers(3, 7))
+        P = np.concatenate([[[0.0, 0.0]], rng.uniform(-4, 4, (m, 2))]).astype(np.float32)
+        V = np.concatenate([[v0], rng.normal(0, 1.0, (m, 2))]).astype(np.float32)
+        G = np.concatenate([[[30 * np.cos(th + rng.normal(0, 0.5)), 30 * np.sin(th + rng.normal(0, 0.5))]],
+                            rng.uniform(-10, 10, (m, 2))]).astype(np.float32)
+        T = np.r_[1, np.zeros(m)].astype(np.uint8)
+        s = scenes.Scene(P, V, G, np.where(T == 1, 1.5, 0.5).astype(np.float32),
+                         np.where(T == 1, 5.0, 1.5).astype(np.float32), T,
+                         scenes.OrcaParams(origin=(-50.0, -50.0), extent=(100.0, 100.0)))
+        r = oracle.step(s, sel=np.array([0]))
+        if (r.flags[0] & 1) == 0 and r.cnt[0] >= 2 and r.tstar[0] < -0.01 and \
+                np.abs(r.vel[0] - V[0]).max() < 1e-5:
+            groups.append(s)
+    shift = [np.array([100.0 * q, 0.0], np.float32) for q in range(count)]
+    cat = lambda f: np.concatenate([f(q, g) for q, g in enumerate(groups)])
+    return scenes.Scene(cat(lambda q, g: g.pos + shift[q]), cat(lambda q, g: g.vel),
+                        cat(lambda q, g: g.goal + shift[q]), cat(lambda q, g: g.radius),
+                        cat(lambda q, g: g.max_speed), cat(lambda q, g: g.type),
+                        scenes.OrcaParams(origin=(-50.0, -50.0),
+                                          extent=(100.0 * count + 100.0, 100.0), cell_size=4.0))
+
+
+def test_vehicle_at_full_speed_on_its_own_half_plane_apex():
+    """The LP optimum at the apex of f = 0 half-planes on the speed circle is
+    feasible (a rounding allowance keeps the 1D intervals from reading empty)."""
+    s = _full_speed_vehicle_apexes()
+    g = gpu_step(s)
+    st = compare(s, g)
+    veh = s.type == 1
+    assert (g["flags"][veh] & 1).sum() == 0
