@@ -221,6 +221,23 @@ int orca_scene_sync_status(orca_scene *scene);
 void orca_scene_destroy(orca_scene *scene);
 
 /*
+ * Remove the agents that have arrived (Sec. 4: agents leave the scene at
+ * their goal; a run ends when all have arrived).  Agent i has arrived when
+ * |g - p|^2 <= r^2, evaluated in FP32 with each difference, product and the
+ * sum rounded in that order, where p is its position now, r its radius and
+ * g its goal, or, for an agent on a route, its last waypoint once that is
+ * its current waypoint.  The kept agents move, in order, to the front of
+ * EVERY agent array of the scene (pos, vel, goal, radius, max_speed, type,
+ * route, wp_idx: the library writes the caller's arrays, including those the
+ * struct declares const), and the scene's agent count becomes *n_kept.
+ * kept_index (device int32[N], or NULL) receives the previous index of each
+ * kept agent in its first *n_kept entries.  The call synchronises `stream`
+ * (the host needs the new count) and drops a captured graph.  Scenes only.
+ */
+int orca_scene_remove_arrived(orca_scene *scene, int *n_kept, int32_t *kept_index,
+                              void *stream);
+
+/*
  * Record the velocity LP's active set of every agent in every following
  * step (NULL to stop): act[N] uint32, caller order, packed as
  *   bits 0-1   0 = projection of the preferred velocity onto the admissible

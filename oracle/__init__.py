@@ -219,6 +219,33 @@ def step(scene, sel=None, vpref_delta=None, state=None, want_lines=False,
     return StepResult(sel_arr, ov, op, owp, onbr, ocnt, ofl, ots, ocond, olines, omask)
 
 
+def arrived(scene, pos, wp_idx=None) -> np.ndarray:
+    """Which agents have reached their goal and leave the scene (Sec. 4:
+    agents are removed on arrival and a run ends when all have arrived).
+
+    Agent i has arrived when |g - p|^2 <= r^2, evaluated in IEEE FP32 with
+    every difference, product and the sum rounded separately (numpy float32
+    arithmetic), where g is its goal, or for an agent on a route its current
+    waypoint once that is the route's last one.
+    """
+    P = np.asarray(pos, dtype=np.float32)
+    G = np.asarray(scene.goal, dtype=np.float32).copy()
+    final = np.ones(P.shape[0], dtype=bool)
+    if scene.route is not None:
+        rt = np.asarray(scene.route)
+        on = np.nonzero(rt >= 0)[0]
+        W = np.asarray(scene.waypoints, dtype=np.float32)
+        wi = np.asarray(wp_idx if wp_idx is not None else scene.wp_idx)[on].astype(np.int64)
+        G[on] = W[rt[on], wi]
+        final[on] = wi == W.shape[1] - 1
+    dx = np.subtract(G[:, 0], P[:, 0], dtype=np.float32)
+    dy = np.subtract(G[:, 1], P[:, 1], dtype=np.float32)
+    d2 = np.add(np.multiply(dx, dx, dtype=np.float32), np.multiply(dy, dy, dtype=np.float32),
+                dtype=np.float32)
+    r = np.asarray(scene.radius, dtype=np.float32)
+    return final & (d2 <= np.multiply(r, r, dtype=np.float32))
+
+
 def rollout(scene, n_steps, vpref_delta=None, fp32_state=True):
     """Run the oracle for ``n_steps`` synchronous steps from the scene's state.
 

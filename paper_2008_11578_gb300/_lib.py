@@ -101,6 +101,7 @@ SIGNATURES = {
     "orca_scene_sync_status": (_I, [_V]),
     "orca_scene_destroy": (None, [_V]),
     "orca_scene_set_debug_active": (_I, [_V, _V]),
+    "orca_scene_remove_arrived": (_I, [_V, ctypes.POINTER(ctypes.c_int), _V, _V]),
     "orca_adjoint_workspace_bytes": (_I, [_V, _I, _I, ctypes.POINTER(ctypes.c_size_t)]),
     "orca_rollout": (_I, [_V, _I, _I, _V, _V, ctypes.c_size_t, _V, _V]),
     "orca_adjoint": (_I, [_V, _I, _I, _V, _V, ctypes.c_size_t, _V, _V, _V, _V, _V, _V, _V]),

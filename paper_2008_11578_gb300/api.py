@@ -172,6 +172,15 @@ def orca_step_noalloc(params: OrcaParams, agents: OrcaAgents, n_steps: int,
                                              _stream_handle(stream), int(bool(synchronize))))
 
 
+def orca_scene_remove_arrived(handle, kept_index=None, stream=None) -> int:
+    """Remove arrived agents in place; returns the new agent count."""
+    n = ctypes.c_int(0)
+    check(_lib.load().orca_scene_remove_arrived(handle, ctypes.byref(n), _ptr(kept_index),
+                                                _stream_handle(stream)),
+          "orca_scene_remove_arrived")
+    return int(n.value)
+
+
 def orca_scene_set_debug_active(handle, act=None):
     """Record every agent's LP active set (uint32[N] on the device)."""
     check(_lib.load().orca_scene_set_debug_active(handle, _ptr(act)),
@@ -358,6 +367,20 @@ class DeviceScene:
             assert vpref_delta.dtype == _torch().float32 and vpref_delta.is_contiguous()
             assert vpref_delta.numel() == 2 * n_steps * self.n
         orca_step(self.handle, n_steps, vpref_delta, stream)
+
+    def remove_arrived(self):
+        """Remove the agents at their goal (the paper's removal on arrival).
+
+        The kept agents are compacted to the front of every device array;
+        ``self.n`` becomes their count (the tensors keep their size, rows
+        ``self.n:`` are stale).  Returns the previous indices of the kept
+        agents (numpy int32)."""
+        torch = _torch()
+        kept = torch.empty(max(self.n, 1), dtype=torch.int32, device=self.device)
+        self.n = orca_scene_remove_arrived(self.handle, kept)
+        if self.dbg is not None:
+            self.enable_debug(active="act" in self.dbg)
+        return kept[:self.n].cpu().numpy()
 
     def capture(self, n_steps: int, vpref_delta=None):
         """Record ``n_steps`` steps into the scene's CUDA graph."""

@@ -43,7 +43,8 @@ struct Layout {
 
 Layout make_layout(size_t n, size_t ncells, size_t n_scenes) {
     Layout L{};
-    size_t nb = (ncells + kScanChunk - 1) / kScanChunk;
+    // block sums of the cell scan, and of the agent scan of orca_scene_remove_arrived
+    size_t nb = (std::max(ncells, n) + kScanChunk - 1) / kScanChunk;
     size_t o = 0;
     auto take = [&](size_t bytes) {
         size_t at = o;
@@ -55,7 +56,7 @@ Layout make_layout(size_t n, size_t ncells, size_t n_scenes) {
     L.start = take((ncells + 1) * 4);
     L.bsum = take((nb + 1) * 4);
     L.key = take(n * 4);
-    L.slot = take(n * 4);
+    L.slot = take((n + 1) * 4);   // + the total of the agent scan
     L.pos0 = take(n * 8);
     L.vel0 = take(n * 8);
     L.pos1 = take(n * 8);
@@ -665,6 +666,49 @@ void orca_scene_destroy(orca_scene* s) {
     if (!s) return;
     drop_graph(s->p);
     delete s;
+}
+
+int orca_scene_remove_arrived(orca_scene* s, int* n_kept, int32_t* kept_index, void* stream) {
+    if (!s || !n_kept) return ORCA_ERR_INVALID_ARG;
+    if (kept_index && !aligned(kept_index, 4)) return ORCA_ERR_INVALID_ARG;
+    Pipeline& P = s->p;
+    const int n = P.n;
+    *n_kept = n;
+    if (n == 0) return ORCA_OK;
+    if ((size_t)n > (size_t)kScanChunk * 1024 * 16) return ORCA_ERR_CAPACITY;
+    cudaStream_t st = (cudaStream_t)stream;
+    const Buffers& B = P.buf;
+    const orca_agents& A = P.agents;
+    const int tb = 256, gb = (n + tb - 1) / tb;
+    const int nb = (n + kScanChunk - 1) / kScanChunk;
+    // keep flags -> exclusive scan (destinations) -> gather into the step
+    // buffers -> copy back to the front of the caller's arrays
+    arrived_kernel<<<gb, tb, 0, st>>>(n, (const float2*)A.pos, (const float2*)A.goal, A.radius,
+                                      A.route, (const float2*)A.waypoints, A.n_waypoints,
+                                      A.wp_idx, B.key);
+    scan_blocks_kernel<<<nb, kScanThreads, 0, st>>>(B.key, B.slot, B.bsum, n);
+    scan_bsum_kernel<<<1, 1024, 0, st>>>(B.bsum, nb);
+    scan_add_kernel<<<(n / 4 + 256) / 256, 256, 0, st>>>(B.slot, B.bsum, n, nb);
+    compact_gather_kernel<<<gb, tb, 0, st>>>(n, B.slot, (const float2*)A.pos, (const float2*)A.vel,
+                                             (const float2*)A.goal, A.radius, A.max_speed, A.type,
+                                             A.route, A.wp_idx, B.pos0, B.vel0, B.pos1, B.vel1,
+                                             B.aux[0], B.aux[1]);
+    uint32_t kept = 0;
+    if (cudaMemcpyAsync(&kept, B.slot + n, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return ORCA_ERR_CUDA;
+    if (kept > 0)
+        compact_scatter_kernel<<<((int)kept + tb - 1) / tb, tb, 0, st>>>(
+            (int)kept, B.pos0, B.vel0, B.pos1, B.vel1, B.aux[0], B.aux[1], (float2*)A.pos,
+            (float2*)A.vel, (float2*)A.goal, (float*)A.radius, (float*)A.max_speed,
+            (uint8_t*)A.type, (int32_t*)A.route, A.wp_idx, kept_index);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        return ORCA_ERR_CUDA;
+    P.n = (int)kept;
+    drop_graph(P);   // a graph recorded for the old count is stale
+    s->adj_steps = -1;
+    *n_kept = (int)kept;
+    return ORCA_OK;
 }
 
 int orca_scene_set_debug_active(orca_scene* s, uint32_t* act) {

@@ -188,6 +188,86 @@ __global__ void scatter_kernel(int n, const uint32_t* __restrict__ key,
     aux_b[s] = aux_a[i];
 }
 
+// ------------------------------------------------------- removal at goal ----
+// keep[i] = 0 when agent i has arrived: |g - p|^2 <= r^2 in FP32, each
+// difference, product and the sum rounded in that order, where g is its goal,
+// or for an agent on a route its last waypoint once that is the current one.
+__global__ void arrived_kernel(int n, const float2* __restrict__ pos,
+                               const float2* __restrict__ goal, const float* __restrict__ radius,
+                               const int32_t* __restrict__ route,
+                               const float2* __restrict__ waypoints, int n_waypoints,
+                               const uint8_t* __restrict__ wp_idx, uint32_t* __restrict__ keep) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float2 p = pos[i];
+    float2 g = goal[i];
+    bool final_target = true;
+    if (route != nullptr && route[i] >= 0) {
+        const int wi = wp_idx[i];
+        final_target = wi == n_waypoints - 1;
+        g = waypoints[(size_t)route[i] * n_waypoints + wi];
+    }
+    const float dx = __fsub_rn(g.x, p.x), dy = __fsub_rn(g.y, p.y);
+    const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    const float r = radius[i];
+    keep[i] = (final_target && d2 <= __fmul_rn(r, r)) ? 0u : 1u;
+}
+
+// Kept agent i moves to dest[i]: its fields are gathered into the step
+// buffers (packed), then copied back to the front of the caller's arrays.
+__global__ void compact_gather_kernel(int n, const uint32_t* __restrict__ dest,
+                                      const float2* __restrict__ pos,
+                                      const float2* __restrict__ vel,
+                                      const float2* __restrict__ goal,
+                                      const float* __restrict__ radius,
+                                      const float* __restrict__ max_speed,
+                                      const uint8_t* __restrict__ type,
+                                      const int32_t* __restrict__ route,
+                                      const uint8_t* __restrict__ wp_idx, float2* __restrict__ t_pos,
+                                      float2* __restrict__ t_vel, float2* __restrict__ t_goal,
+                                      float2* __restrict__ t_rv, uint2* __restrict__ t_misc,
+                                      uint2* __restrict__ t_orig) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t d = dest[i];
+    if (dest[i + 1] == d) return;   // not kept (exclusive scan did not advance)
+    t_pos[d] = pos[i];
+    t_vel[d] = vel[i];
+    t_goal[d] = goal[i];
+    t_rv[d] = make_float2(radius[i], max_speed[i]);
+    t_misc[d] = make_uint2(route ? (uint32_t)route[i] : 0u,
+                           (uint32_t)type[i] | ((wp_idx ? (uint32_t)wp_idx[i] : 0u) << 8));
+    t_orig[d] = make_uint2((uint32_t)i, 0u);
+}
+
+__global__ void compact_scatter_kernel(int kept, const float2* __restrict__ t_pos,
+                                       const float2* __restrict__ t_vel,
+                                       const float2* __restrict__ t_goal,
+                                       const float2* __restrict__ t_rv,
+                                       const uint2* __restrict__ t_misc,
+                                       const uint2* __restrict__ t_orig, float2* __restrict__ pos,
+                                       float2* __restrict__ vel, float2* __restrict__ goal,
+                                       float* __restrict__ radius, float* __restrict__ max_speed,
+                                       uint8_t* __restrict__ type, int32_t* __restrict__ route,
+                                       uint8_t* __restrict__ wp_idx,
+                                       int32_t* __restrict__ kept_index) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= kept) return;
+    pos[d] = t_pos[d];
+    vel[d] = t_vel[d];
+    goal[d] = t_goal[d];
+    const float2 rv = t_rv[d];
+    radius[d] = rv.x;
+    max_speed[d] = rv.y;
+    const uint2 m = t_misc[d];
+    type[d] = (uint8_t)(m.y & 0xffu);
+    if (route != nullptr) {
+        route[d] = (int32_t)m.x;
+        wp_idx[d] = (uint8_t)(m.y >> 8);
+    }
+    if (kept_index != nullptr) kept_index[d] = (int32_t)t_orig[d].x;
+}
+
 // ----------------------------------------------------------------- solve ----
 // One thread per agent (sorted slot s).  The neighbour list and then the
 // lines are kept in dynamic shared memory (k float4 slots per thread), slot i

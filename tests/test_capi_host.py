@@ -156,3 +156,9 @@ def test_batch_validation_on_host():
     assert L.orca_scene_graph_launch(None, None) == 1
     assert L.orca_batch_sync_status(None) == 1
     L.orca_batch_destroy(None)
+
+
+def test_removal_rejects_null_arguments():
+    L = _lib.load()
+    n = ctypes.c_int()
+    assert L.orca_scene_remove_arrived(None, ctypes.byref(n), None, None) == 1

@@ -550,3 +550,19 @@ def test_responsibility_zero_keeps_constraint_through_own_velocity():
     """f = 0 (car|person): the half-plane passes through v_A itself (Sec. 3.1)."""
     L = oracle.pair_line([0, 0], [1.0, 0.2], 1.5, [3, 0.5], [-1, 0], 0.5, 0.0, 5.0, 0.25, False)
     assert np.allclose(L[:2], [1.0, 0.2], atol=0)
+
+
+def test_arrival_rule_boundaries():
+    """The removal rule at its exact FP32 boundary: |g - p|^2 <= r^2 with
+    each operation rounded; routed agents only at their last waypoint."""
+    s = scenes.waypoint_square(n_ped=3, n_veh=1, side=10.0, n_wp=2, seed=0)
+    s.radius[:] = np.float32(0.5)
+    P = np.zeros((4, 2), np.float32)
+    s.goal[:3] = np.array([[0.5, 0.0], [np.nextafter(np.float32(0.5), np.float32(1)), 0.0],
+                           [0.3, 0.4]], np.float32)
+    s.waypoints[0] = np.array([[0.0, 0.0], [0.1, 0.0]], np.float32)
+    got = oracle.arrived(s, P, np.array([0, 0, 0, 0], np.uint8))
+    # exactly r away: arrived; one ulp farther: not; 3-4-5 triangle scaled: d^2 = 0.25 = r^2
+    assert got[:3].tolist() == [True, False, True]
+    assert not got[3]                                  # on its first waypoint
+    assert oracle.arrived(s, P, np.array([0, 0, 0, 1], np.uint8))[3]
