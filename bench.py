@@ -219,14 +219,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(scene, cfg, budget_s=12.0):
+def cpu_baseline(scene, cfg, budget_s=15.0):
     """Oracle timed on a bounded sample of the same workload (rank 0, N=1)."""
     import numpy as np
 
     import oracle
     oracle.build()
     rng = np.random.default_rng(1)
-    probe = np.sort(rng.choice(scene.n, min(scene.n, 200), replace=False))
+    # a probe large enough to keep every host core busy, so that the
+    # per-agent cost it measures holds for the sample
+    probe = np.sort(rng.choice(scene.n, min(scene.n, 4000), replace=False))
     t0 = time.perf_counter()
     oracle.step(scene, sel=probe)
     per_agent = (time.perf_counter() - t0) / len(probe)
