@@ -357,6 +357,34 @@ def measure_adjoint(dev, n_steps=40, ckpt_every=8, reps=5):
     return out
 
 
+def measure_lp_schemes(scene, dev, cell, block, pos, vel, steps=5):
+    """The per-thread incremental LP against the paper's work-unit batch LP
+    (Sec. 3), same workload, launch shape and start state (``pos``/``vel``):
+    median solve-kernel time over ``steps`` single steps (the two agree to
+    FP32 rounding)."""
+    import torch
+
+    from paper_2008_11578_gb300 import api
+    out = {}
+    for name, flags in (("per_thread", 0), ("work_units", api.LP_WORK_UNITS)):
+        ds = api.DeviceScene(scene, dev, cell_size=cell, block_size=block, flags=flags)
+        p0, v0 = pos.clone(), vel.clone()
+        b, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        api.orca_scene_set_solve_events(ds.handle, b, e)
+        ts = []
+        for r in range(steps + 1):
+            ds.pos.copy_(p0)
+            ds.vel.copy_(v0)
+            ds.step(1)
+            torch.cuda.synchronize()
+            if r:
+                ts.append(api.event_elapsed_ms(b, e))
+        out[name + "_solve_ms"] = statistics.median(ts)
+        ds.close()
+    out["work_units_over_per_thread"] = out["work_units_solve_ms"] / out["per_thread_solve_ms"]
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -509,6 +537,12 @@ def run_ours(args):
             "roofline": roofline, "roofline_binning": roofline_binning, "e2e": e2e,
             "status": status,
             "hbm_peak_gbs": peaks.get("hbm_gbs")}
+    if not args.no_ablation:
+        line["lp_scheme_ablation"] = dict(
+            measure_lp_schemes(scene, dev, float(ds.params.cell_size),
+                               int(ds.params.block_size), ds.pos, ds.vel),
+            workload=cfg["workload"],
+            state=f"after the {args.warmup + args.steps} warm-up and timed steps")
     if not args.no_batched:
         line["batched"] = measure_batched(dev, flush)
     if not args.no_adjoint:
@@ -535,6 +569,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -60,6 +60,11 @@ extern "C" {
 
 /* debug_flags bits */
 #define ORCA_DEBUG_NONE 0u
+/* Solve the 2D LPs with the batch-LP load balancing the paper uses (Sec. 3,
+   LP paragraphs: re-solves split into work units that every thread of a
+   block shares) instead of one thread per LP.  Results agree to FP32
+   rounding.  Other bits are rejected. */
+#define ORCA_FLAG_LP_WORK_UNITS 2u
 
 /*
  * Global parameters of one scene (Sec. 3 and 3.1).
@@ -75,7 +80,7 @@ extern "C" {
  *                   changes
  *   origin_x/y, grid_nx/ny   grid box; agents outside clamp to edge cells
  *   block_size      threads per block of the solve kernel (0 = 128)
- *   debug_flags     ORCA_DEBUG_* bits (0)
+ *   debug_flags     ORCA_DEBUG_NONE or ORCA_FLAG_LP_WORK_UNITS
  */
 typedef struct orca_params {
     float neighbor_dist;

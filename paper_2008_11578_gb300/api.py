@@ -33,7 +33,11 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def make_params(p, cell_size: float | None = None, block_size: int = 0) -> OrcaParams:
+LP_WORK_UNITS = 2   # orca_params.debug_flags: the paper's work-unit batch LP
+
+
+def make_params(p, cell_size: float | None = None, block_size: int = 0,
+                flags: int = 0) -> OrcaParams:
     """orca_params from a :class:`scenes.OrcaParams` (grid from its box)."""
     c = float(p.cell_size if cell_size is None else cell_size)
     nx, ny = p.grid_dims(c)
@@ -52,7 +56,7 @@ def make_params(p, cell_size: float | None = None, block_size: int = 0) -> OrcaP
     cp.grid_nx = int(nx)
     cp.grid_ny = int(ny)
     cp.block_size = int(block_size)
-    cp.debug_flags = 0
+    cp.debug_flags = int(flags)
     return cp
 
 
@@ -297,7 +301,8 @@ class DeviceScene:
     and ``waypoints`` are read-only inputs.
     """
 
-    def __init__(self, scene, device="cuda", cell_size=None, block_size=0, debug=False):
+    def __init__(self, scene, device="cuda", cell_size=None, block_size=0, debug=False,
+                 flags=0):
         torch = _torch()
         self.device = torch.device(device)
         self.scene = scene
@@ -319,7 +324,7 @@ class DeviceScene:
             self.route = t(scene.route, torch.int32)
             self.waypoints = t(scene.waypoints.reshape(-1, 2), torch.float32)
             self.wp_idx = t(scene.wp_idx, torch.uint8)
-        self.params = make_params(scene.params, cell_size, block_size)
+        self.params = make_params(scene.params, cell_size, block_size, flags)
         self.ws_bytes = orca_workspace_bytes(self.params, self.n)
         self.workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
         a = OrcaAgents()

@@ -120,6 +120,7 @@ int check_params(const orca_params* p) {
         return ORCA_ERR_CAPACITY;
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 128 || p->block_size % 32))
         return ORCA_ERR_INVALID_ARG;
+    if (p->debug_flags & ~(unsigned)ORCA_FLAG_LP_WORK_UNITS) return ORCA_ERR_INVALID_ARG;
     return ORCA_OK;
 }
 
@@ -193,6 +194,9 @@ cudaError_t prepare_solve(size_t smem) {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(solve_kernel<SRC, MODE_RECORD>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(solve_kernel<SRC, MODE_PLAIN, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return e;
 }
 
@@ -201,12 +205,13 @@ void launch_solve(int mode, int grid, int block, size_t smem, cudaStream_t st, i
                   const float2* pos, const float2* vel, const uint2* aux, const uint32_t* start,
                   AgentIn ain, const float2* vpd, StepOut out, DebugOut dbg,
                   unsigned long long* counters) {
-#define ORCA_SOLVE(M)                                                                    \
-    solve_kernel<SRC, M><<<grid, block, smem, st>>>(n, src, pos, vel, aux, start, ain, vpd, \
-                                                     out, dbg, counters)
-    if (mode == MODE_COUNT) ORCA_SOLVE(MODE_COUNT);
-    else if (mode == MODE_RECORD) ORCA_SOLVE(MODE_RECORD);
-    else ORCA_SOLVE(MODE_PLAIN);
+#define ORCA_SOLVE(M, W)                                                                    \
+    solve_kernel<SRC, M, W><<<grid, block, smem, st>>>(n, src, pos, vel, aux, start, ain, vpd, \
+                                                        out, dbg, counters)
+    if (mode == MODE_COUNT) ORCA_SOLVE(MODE_COUNT, false);
+    else if (mode == MODE_RECORD) ORCA_SOLVE(MODE_RECORD, false);
+    else if (mode == MODE_WORK_UNITS) ORCA_SOLVE(MODE_PLAIN, true);
+    else ORCA_SOLVE(MODE_PLAIN, false);
 #undef ORCA_SOLVE
 }
 
@@ -221,6 +226,7 @@ struct Pipeline {
     int kcap;
     int block;
     int n_scenes;
+    unsigned flags;   // orca_params.debug_flags
     Layout lay;
     char* ws;
     Buffers buf;
@@ -245,7 +251,8 @@ struct SameDebug {
 
 int step_mode(const Pipeline& P) {
     if (P.counters != nullptr) return MODE_COUNT;
-    return P.dbg.act != nullptr ? MODE_RECORD : MODE_PLAIN;
+    if (P.dbg.act != nullptr) return MODE_RECORD;
+    return (P.flags & ORCA_FLAG_LP_WORK_UNITS) ? MODE_WORK_UNITS : MODE_PLAIN;
 }
 
 // Enqueue the load and n_steps steps.  dbg_for(t) gives the solve
@@ -381,8 +388,10 @@ int launch_graph(Pipeline& P, cudaStream_t st) {
 }
 
 void init_pipeline(Pipeline& P, const orca_agents* agents, int ncells, int kcap, int block,
-                   int n_scenes, const Layout& lay, void* workspace, int k_stride) {
+                   int n_scenes, const Layout& lay, void* workspace, int k_stride,
+                   unsigned flags) {
     P.agents = *agents;
+    P.flags = flags;
     P.n = agents->n_agents;
     P.ncells = ncells;
     P.nblocks = (ncells + kScanChunk - 1) / kScanChunk;
@@ -590,7 +599,8 @@ int orca_scene_create(const orca_params* params, const orca_agents* agents, void
     if (!s) return ORCA_ERR_CAPACITY;
     s->params = *params;
     init_pipeline(s->p, agents, (int)ncells, kcap_for(params->max_neighbors),
-                  params->block_size, 0, lay, workspace, params->max_neighbors);
+                  params->block_size, 0, lay, workspace, params->max_neighbors,
+                  params->debug_flags);
     s->p.one = scene_dev(params, 0, s->p.n, 0);
     s->adj_steps = -1;
     s->adj_every = 0;
@@ -963,7 +973,7 @@ int orca_batch_create(const orca_params* params, int n_scenes, const int* offset
     b->n_scenes = n_scenes;
     b->kmax = kmax;
     init_pipeline(b->p, agents, (int)ncells, kcap_for(kmax), params[0].block_size, n_scenes, lay,
-                  workspace, kmax);
+                  workspace, kmax, params[0].debug_flags);
     bool ok = cudaMemset(b->p.buf.err, 0, 16) == cudaSuccess &&
               cudaMemcpy(b->p.buf.scenes, table.data(), table.size() * sizeof(SceneDev),
                          cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -1080,7 +1090,7 @@ extern "C" int orca_step_noalloc(const orca_params* params, const orca_agents* a
     // a pipeline over the scratch area, held on the host stack
     Pipeline P;
     init_pipeline(P, agents, (int)ncells, kcap_for(params->max_neighbors), params->block_size,
-                  0, L, w, params->max_neighbors);
+                  0, L, w, params->max_neighbors, params->debug_flags);
     P.one = scene_dev(params, 0, n, 0);
     st = prepare(P);
     if (st != ORCA_OK) return st;

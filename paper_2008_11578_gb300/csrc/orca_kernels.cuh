@@ -107,6 +107,8 @@ struct DebugOut {
 
 // Variants of the solve kernel: plain, with work tallies, with the active set
 constexpr int MODE_PLAIN = 0, MODE_COUNT = 1, MODE_RECORD = 2;
+// host-side choice of the plain variant with the paper's work-unit LP
+constexpr int MODE_WORK_UNITS = 3;
 
 // Work tallies of the counting variant of the solve kernel:
 // [0] candidate key tests, [1] ORCA lines built, [2] LP pair evaluations

@@ -461,4 +461,123 @@ __device__ __forceinline__ int solve_velocity(const float4* __restrict__ L, int 
     return 1;
 }
 
+// ---------------------------------------------------------------------------
+// The paper's batch-LP load balancing, for comparison (Sec. 3, LP
+// paragraphs): each thread owns one agent's LP and scans its constraints
+// incrementally; when the current optimum violates constraint i, the re-solve
+// on line i is split into work units, one per earlier constraint j, and every
+// thread of the block takes its share of all pending units, whether or not its
+// own LP needs a re-solve.  The block runs the scan in lockstep over i.  Each
+// unit yields one bound of line i's interval, merged with shared-memory
+// atomics; min and max are exact, so the interval equals the per-thread
+// solver's up to how the compiler contracts the bound's multiply-adds.
+// Agents whose 2D LP is empty continue with the per-thread least-penetration
+// LP.
+// ---------------------------------------------------------------------------
+
+// order-preserving map of floats to ints (for atomic min/max)
+__device__ __forceinline__ int f2o(float f) {
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float o2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+constexpr int kWorkUnitMaxBlock = 128;
+
+// All threads of the block must call this (inactive ones with n = 0).
+// lines_base is the block's line array (agent a, line j at [j * B + a]).
+__device__ __forceinline__ int solve_velocity_work_units(const float4* __restrict__ lines_base,
+                                                         int n, float vmax, float vpx,
+                                                         float vpy, float& vx, float& vy,
+                                                         float& tstar, int& work) {
+    __shared__ int s_tl[kWorkUnitMaxBlock], s_tr[kWorkUnitMaxBlock];
+    __shared__ int s_empty[kWorkUnitMaxBlock], s_list[kWorkUnitMaxBlock];
+    __shared__ float s_tol[kWorkUnitMaxBlock];
+    __shared__ int s_n, s_kmax;
+    const int tid = threadIdx.x, B = blockDim.x;
+    const float4* L = lines_base + tid;
+    const float tol = lp_tol(vmax);
+    tstar = 0.0f;
+    const float vp2 = vpx * vpx + vpy * vpy;
+    if (vp2 > vmax * vmax) {
+        const float sc = vmax / sqrtf(vp2);
+        vx = vpx * sc;
+        vy = vpy * sc;
+    } else {
+        vx = vpx;
+        vy = vpy;
+    }
+    s_tol[tid] = tol;
+    if (tid == 0) {
+        s_kmax = 0;
+        s_n = 0;
+    }
+    __syncthreads();
+    atomicMax(&s_kmax, n);
+    __syncthreads();
+    const int kmax = s_kmax;
+    bool live = true;
+    for (int i = 0; i < kmax; ++i) {
+        bool need = false;
+        float4 li = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (live && i < n) {
+            li = L[i * B];
+            need = penetration(li, vx, vy) > 0.0f;
+        }
+        if (need) {
+            const float dot = li.x * li.z + li.y * li.w;
+            const float disc = dot * dot + vmax * vmax - (li.x * li.x + li.y * li.y);
+            const float sq = sqrtf(fmaxf(disc, 0.0f));
+            s_tl[tid] = f2o(-dot - sq);
+            s_tr[tid] = f2o(-dot + sq);
+            s_empty[tid] = disc < -tol * (1.0f + vmax) ? 1 : 0;
+            s_list[atomicAdd(&s_n, 1)] = tid;
+        }
+        __syncthreads();
+        const int units = s_n * i;   // one unit = (agent needing a re-solve, earlier line)
+        for (int w = tid; w < units; w += B) {
+            const int q = w / i;
+            const int a = s_list[q], j = w - q * i;
+            const float4 la = lines_base[i * B + a], lj = lines_base[j * B + a];
+            const float den = la.z * lj.w - la.w * lj.z;                     // det(d_i, d_j)
+            const float num = lj.z * (la.y - lj.y) - lj.w * (la.x - lj.x);   // det(d_j, P_i - P_j)
+            if (den == 0.0f) {
+                if (num < -s_tol[a]) atomicOr(&s_empty[a], 1);
+            } else {
+                const float t = __fdividef(num, den);
+                if (den > 0.0f) atomicMin(&s_tr[a], f2o(t));
+                else atomicMax(&s_tl[a], f2o(t));
+            }
+        }
+        work += units > 0 ? (units + B - 1) / B : 0;
+        __syncthreads();
+        if (need) {
+            const float tl = o2f(s_tl[tid]), tr = o2f(s_tr[tid]);
+            if (s_empty[tid] || tl > tr + tol) {
+                live = false;
+            } else {
+                const float t0 = li.z * (vpx - li.x) + li.w * (vpy - li.y);
+                const float t = fminf(fmaxf(t0, tl), tr);
+                vx = li.x + t * li.z;
+                vy = li.y + t * li.w;
+            }
+        }
+        if (tid == 0) s_n = 0;
+        __syncthreads();
+    }
+    if (live) return 0;
+    float v3x, v3y;
+    uint32_t act = 0u;
+    const float t3 = lp3_min_penetration(L, B, n, vmax, v3x, v3y, work, act);
+    tstar = t3;
+    vx = v3x;
+    vy = v3y;
+    float ox, oy;
+    if (valley_tie_break(L, B, n, t3, vmax, vpx, vpy, v3x, v3y, ox, oy, work, act)) {
+        vx = ox;
+        vy = oy;
+    }
+    return 1;
+}
+
 }  // namespace orca

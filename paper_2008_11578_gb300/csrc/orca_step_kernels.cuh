@@ -274,7 +274,10 @@ __global__ void compact_scatter_kernel(int kept, const float2* __restrict__ t_po
 // of thread t at [i * blockDim.x + t] (conflict-free float4).
 // MODE_COUNT adds work tallies (algorithmic FLOP accounting) and
 // MODE_RECORD the LP's active set; both are dead code in MODE_PLAIN.
-template <class SRC, int MODE>
+// WORK_UNITS solves the 2D LPs with the paper's block-cooperative work units
+// (comparison only); every thread of a block then takes part to the end of
+// the LP, lanes past the last agent shadowing it and writing nothing.
+template <class SRC, int MODE, bool WORK_UNITS = false>
 __global__ void __launch_bounds__(128)
 solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __restrict__ vel,
              const uint2* __restrict__ aux, const uint32_t* __restrict__ cstart,
@@ -283,8 +286,10 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     extern __shared__ float4 smem_lines[];
     const int stride = blockDim.x;
     float4* L = smem_lines + threadIdx.x;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
+    const int s_raw = blockIdx.x * blockDim.x + threadIdx.x;
+    if (!WORK_UNITS && s_raw >= n) return;
+    const bool active = s_raw < n;
+    const int s = active ? s_raw : n - 1;
     const SceneDev sc = src.get(s);
     const float2 p = pos[s];
     const float2 v = vel[s];
@@ -375,15 +380,17 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         const int rt = ain.route[o];
         if (rt >= 0) {
             int wi = ain.wp_idx[o];
-            if (dbg.swp != nullptr) dbg.swp[o] = (uint8_t)wi;
+            if (active && dbg.swp != nullptr) dbg.swp[o] = (uint8_t)wi;
             const float2* W = ain.waypoints + (size_t)rt * ain.n_waypoints;
             float2 w = W[wi];
             float wdx = __fsub_rn(w.x, p.x), wdy = __fsub_rn(w.y, p.y);
             float w2 = __fadd_rn(__fmul_rn(wdx, wdx), __fmul_rn(wdy, wdy));
             if (wi < ain.n_waypoints - 1 && w2 <= __fmul_rn(r, r)) ++wi;
             g = W[wi];
-            ain.wp_idx[o] = (uint8_t)wi;
-            if (dbg.wp_used != nullptr) dbg.wp_used[o] = (uint8_t)wi;
+            if (active) {
+                ain.wp_idx[o] = (uint8_t)wi;
+                if (dbg.wp_used != nullptr) dbg.wp_used[o] = (uint8_t)wi;
+            }
         }
     }
     float vpx = 0.0f, vpy = 0.0f;
@@ -404,7 +411,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
 
     // ---- one ORCA half-plane per neighbour (Sec. 3.1) ----
     // Constraint m is the m-th nearest; its line replaces its list entry.
-    if (dbg.nbr != nullptr) {
+    if (active && dbg.nbr != nullptr) {
         int32_t* nb = dbg.nbr + (size_t)o * dbg.k_stride;
         for (int m = 0; m < dbg.k_stride; ++m)
             nb[m] = m < cnt ? __float_as_int(L[m * stride].z) : -1;
@@ -435,7 +442,11 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     float vx, vy, tstar;
     uint32_t act = 0u;
     const int infeasible =
-        solve_velocity(L, stride, cnt, vmax, vpx, vpy, vx, vy, tstar, work, act);
+        WORK_UNITS
+            ? solve_velocity_work_units(smem_lines, active ? cnt : 0, vmax, vpx, vpy, vx, vy,
+                                        tstar, work)
+            : solve_velocity(L, stride, cnt, vmax, vpx, vpy, vx, vy, tstar, work, act);
+    if (!active) return;
     const uint8_t flags = (uint8_t)(infeasible | (any_overlap ? 4 : 0));
 
     // ---- integrate ----

@@ -23,11 +23,13 @@ def half_ulp(x):
     return 0.5 * (np.nextafter(x, np.float32(np.inf)) - x).astype(np.float64)
 
 
-def gpu_step(scene, n_steps=1, cell_size=None, block_size=0, vpref_delta=None, debug=True):
+def gpu_step(scene, n_steps=1, cell_size=None, block_size=0, vpref_delta=None, debug=True,
+             flags=0):
     """Run the CUDA path on a copy of ``scene``; returns numpy outputs."""
     import torch
     from paper_2008_11578_gb300 import api
-    ds = api.DeviceScene(scene, "cuda", cell_size=cell_size, block_size=block_size, debug=debug)
+    ds = api.DeviceScene(scene, "cuda", cell_size=cell_size, block_size=block_size, debug=debug,
+                         flags=flags)
     vpd = None
     if vpref_delta is not None:
         vpd = torch.as_tensor(np.ascontiguousarray(vpref_delta, dtype=np.float32), device="cuda")

@@ -54,7 +54,8 @@ def test_workspace_bytes_and_parameter_validation():
                       (dict(time_horizon=float("nan")), 1), (dict(cell_size=0.0), 1),
                       (dict(max_neighbors=-1), 1), (dict(max_neighbors=33), 5),
                       (dict(grid_nx=0), 1), (dict(grid_nx=1 << 14, grid_ny=1 << 14), 5),
-                      (dict(block_size=48), 1), (dict(block_size=256), 1)]:
+                      (dict(block_size=48), 1), (dict(block_size=256), 1),
+                      (dict(debug_flags=1), 1), (dict(debug_flags=6), 1)]:
         p = _params(**bad)
         assert L.orca_workspace_bytes(ctypes.byref(p), 10, ctypes.byref(out)) == code, bad
     p = _params()
