@@ -81,6 +81,17 @@ extern "C" {
  *   origin_x/y, grid_nx/ny   grid box; agents outside clamp to edge cells
  *   block_size      threads per block of the solve kernel (0 = 128)
  *   debug_flags     ORCA_DEBUG_NONE or ORCA_FLAG_LP_WORK_UNITS
+ *   vehicle_turn_rate, vehicle_accel   kinematic limits of vehicles (type 1),
+ *                   rad/s and m/s^2, 0 = off (default).  The paper names such
+ *                   extra linear constraints as its extension for vehicles
+ *                   (Sec. 5).  A vehicle moving at |v| >= 0.1 m/s gets two
+ *                   half-planes through the origin that keep the new
+ *                   velocity within +-turn_rate*dt of its heading (turn_rate*dt
+ *                   < pi/2), and one half-plane v . h <= |v| + accel*dt along its
+ *                   heading h; a slower vehicle gets only the latter, along
+ *                   its preferred velocity.  They enter the same LP (and the
+ *                   least-penetration fallback) after the ORCA half-planes.
+ *                   Not differentiated: orca_rollout/orca_adjoint refuse them.
  */
 typedef struct orca_params {
     float neighbor_dist;
@@ -95,6 +106,8 @@ typedef struct orca_params {
     int grid_ny;
     int block_size;
     unsigned debug_flags;
+    float vehicle_turn_rate;
+    float vehicle_accel;
 } orca_params;
 
 /*

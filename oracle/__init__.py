@@ -79,6 +79,7 @@ def lib():
                 [ctypes.c_int] + [_D] * 8 + [_U8, _I32, _D, _D, ctypes.c_int, _U8,
                                              _D, _D, ctypes.c_double, ctypes.c_int,
                                              ctypes.c_double, ctypes.c_double, _D,
+                                             ctypes.c_double, ctypes.c_double,
                                              ctypes.c_int, _I32, _D, _D, _U8, _I32,
                                              _I32, _U8, _D, _D, _D, _U32])
             L.oracle_step.restype = ctypes.c_int
@@ -211,7 +212,9 @@ def step(scene, sel=None, vpref_delta=None, state=None, want_lines=False,
         _p(rad, _D), _p(vm, _D), _p(ty, _U8), _p(route, _I32), _p(wpx, _D),
         _p(wpy, _D), n_wp, _p(wpi, _U8), _p(dvx, _D), _p(dvy, _D),
         float(np.float32(prm.neighbor_dist)), k, float(np.float32(prm.time_horizon)),
-        float(np.float32(prm.dt)), _p(f4, _D), ns, _p(sel_arr, _I32), _p(ov, _D),
+        float(np.float32(prm.dt)), _p(f4, _D),
+        float(np.float32(getattr(prm, "vehicle_turn_rate", 0.0))),
+        float(np.float32(getattr(prm, "vehicle_accel", 0.0))), ns, _p(sel_arr, _I32), _p(ov, _D),
         _p(op, _D), _p(owp, _U8), _p(onbr, _I32), _p(ocnt, _I32), _p(ofl, _U8),
         _p(ots, _D), _p(ocond, _D), _p(olines, _D), _p(omask, _U32))
     if rc != 0:

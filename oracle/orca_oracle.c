@@ -527,7 +527,8 @@ int oracle_step(int n, const double *px, const double *py, const double *vx,
                 const int32_t *route, const double *wpx, const double *wpy,
                 int n_wp, const uint8_t *wp_idx, const double *dvx,
                 const double *dvy, double neighbor_dist, int k, double tau,
-                double dt, const double *f4, int n_sel, const int32_t *sel,
+                double dt, const double *f4, double turn_rate, double accel,
+                int n_sel, const int32_t *sel,
                 double *out_v, double *out_p, uint8_t *out_wp, int32_t *out_nbr,
                 int32_t *out_cnt, uint8_t *out_flags, double *out_tstar,
                 double *out_cond, double *out_lines, uint32_t *out_mask)
@@ -588,7 +589,7 @@ int oracle_step(int n, const double *px, const double *py, const double *vx,
             vpy += dvy[a];
         }
         /* one ORCA line per neighbour */
-        oline L[64];
+        oline L[64 + 3];   /* k ORCA lines + up to 3 kinematic ones */
         int any_overlap = 0;
         for (int m = 0; m < cnt; ++m) {
             int b = bi[m];
@@ -601,9 +602,48 @@ int oracle_step(int n, const double *px, const double *py, const double *vx,
             pair_line(px[a], py[a], vx[a], vy[a], radius[a], px[b], py[b], vx[b],
                       vy[b], radius[b], f, tau, dt, overlap, &L[m]);
         }
+        /* vehicles' kinematic half-planes (the paper's proposed extension,
+           Sec. 5), after the ORCA ones: for a moving vehicle (|v| >= 0.1 m/s,
+           an FP32 decision) the new heading stays within +-turn_rate*dt of the
+           current one (two half-planes through the origin), and the forward
+           speed grows by at most accel*dt (v . h <= |v| + accel dt); a slower
+           vehicle gets only the latter, along its preferred velocity */
+        int nl = cnt;
+        if (type[a] != 0 && (turn_rate > 0.0 || accel > 0.0)) {
+            float fvx = (float)vx[a], fvy = (float)vy[a];
+            float sx = fvx * fvx, sy = fvy * fvy;
+            float sp2f = sx + sy;
+            int moving = sp2f >= 0.01f;
+            double hx = 0.0, hy = 0.0, sp = 0.0;
+            if (moving) {
+                sp = sqrt(vx[a] * vx[a] + vy[a] * vy[a]);
+                hx = vx[a] / sp;
+                hy = vy[a] / sp;
+            } else {
+                double pl = sqrt(vpx * vpx + vpy * vpy);
+                if (pl > 0.0) { hx = vpx / pl; hy = vpy / pl; }
+            }
+            if (moving && turn_rate > 0.0) {
+                double th = turn_rate * dt, c = cos(th), sn = sin(th);
+                /* left ray R(+th) h: admissible to its right, d = -R(+th) h */
+                L[nl].px = 0.0; L[nl].py = 0.0;
+                L[nl].dx = -(c * hx - sn * hy); L[nl].dy = -(sn * hx + c * hy);
+                ++nl;
+                /* right ray R(-th) h: admissible to its left */
+                L[nl].px = 0.0; L[nl].py = 0.0;
+                L[nl].dx = c * hx + sn * hy; L[nl].dy = -sn * hx + c * hy;
+                ++nl;
+            }
+            if (accel > 0.0 && (hx != 0.0 || hy != 0.0)) {
+                double smax = sp + accel * dt;
+                L[nl].px = smax * hx; L[nl].py = smax * hy;
+                L[nl].dx = -hy; L[nl].dy = hx;
+                ++nl;
+            }
+        }
         double nvx, nvy, ts, cond;
         uint32_t mask;
-        int fl = lp_solve(L, cnt, vmax[a], vpx, vpy, &nvx, &nvy, &ts, &cond, &mask);
+        int fl = lp_solve(L, nl, vmax[a], vpx, vpy, &nvx, &nvy, &ts, &cond, &mask);
         if (any_overlap) fl |= 4;
         out_v[2 * s] = nvx;
         out_v[2 * s + 1] = nvy;

@@ -57,6 +57,8 @@ def make_params(p, cell_size: float | None = None, block_size: int = 0,
     cp.grid_ny = int(ny)
     cp.block_size = int(block_size)
     cp.debug_flags = int(flags)
+    cp.vehicle_turn_rate = float(getattr(p, "vehicle_turn_rate", 0.0))
+    cp.vehicle_accel = float(getattr(p, "vehicle_accel", 0.0))
     return cp
 
 

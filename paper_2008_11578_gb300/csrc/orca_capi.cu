@@ -121,6 +121,10 @@ int check_params(const orca_params* p) {
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 128 || p->block_size % 32))
         return ORCA_ERR_INVALID_ARG;
     if (p->debug_flags & ~(unsigned)ORCA_FLAG_LP_WORK_UNITS) return ORCA_ERR_INVALID_ARG;
+    if (!std::isfinite(p->vehicle_turn_rate) || !std::isfinite(p->vehicle_accel) ||
+        p->vehicle_turn_rate < 0.0f || p->vehicle_accel < 0.0f ||
+        (double)p->vehicle_turn_rate * (double)p->dt >= 1.5707963267948966)
+        return ORCA_ERR_INVALID_ARG;
     return ORCA_OK;
 }
 
@@ -173,13 +177,24 @@ SceneDev scene_dev(const orca_params* p, int agent_off, int n, int cell_off) {
     s.f01 = p->f[0][1];
     s.f10 = p->f[1][0];
     s.f11 = p->f[1][1];
+    const double th = (double)p->vehicle_turn_rate * (double)p->dt;
+    s.kin_turn = p->vehicle_turn_rate > 0.0f;
+    s.kin_accel = p->vehicle_accel > 0.0f;
+    s.cos_turn = (float)std::cos(th);
+    s.sin_turn = (float)std::sin(th);
+    volatile float a = p->vehicle_accel;
+    s.accel_dt = a * p->dt;
     return s;
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? ORCA_OK : ORCA_ERR_CUDA; }
 
-// float4 slots per thread: the neighbour list, then the lines
-int kcap_for(int k) { return std::max(k, 1); }
+// float4 slots per thread: the neighbour list, then the lines (plus the
+// vehicles' kinematic half-planes)
+int kcap_for(int k, bool kin) { return std::max(k, 1) + (kin ? kKinLines : 0); }
+bool kinematic(const orca_params* p) {
+    return p->vehicle_turn_rate > 0.0f || p->vehicle_accel > 0.0f;
+}
 
 // More than 48 KB of dynamic shared memory needs an explicit opt-in, set
 // once per scene/batch on its device (outside any stream capture).
@@ -414,12 +429,13 @@ void init_pipeline(Pipeline& P, const orca_agents* agents, int ncells, int kcap,
 // Host-side checks of a batch description; fills the total cell count and
 // the largest k.
 int check_batch(const orca_params* params, int n_scenes, const int* offsets, int n_agents,
-                size_t* ncells_out, int* kmax_out) {
+                size_t* ncells_out, int* kmax_out, bool* kin_out = nullptr) {
     if (!params || !offsets || n_scenes < 1) return ORCA_ERR_INVALID_ARG;
     if (n_scenes > ORCA_MAX_SCENES) return ORCA_ERR_CAPACITY;
     if (offsets[0] != 0 || offsets[n_scenes] != n_agents) return ORCA_ERR_INVALID_ARG;
     size_t ncells = 0;
     int kmax = 0;
+    bool kin = false;
     for (int s = 0; s < n_scenes; ++s) {
         int st = check_params(params + s);
         if (st != ORCA_OK) return st;
@@ -430,9 +446,11 @@ int check_batch(const orca_params* params, int n_scenes, const int* offsets, int
         ncells += (size_t)params[s].grid_nx * (size_t)params[s].grid_ny;
         if (ncells > (size_t)ORCA_MAX_CELLS) return ORCA_ERR_CAPACITY;
         kmax = std::max(kmax, params[s].max_neighbors);
+        kin = kin || kinematic(params + s);
     }
     *ncells_out = ncells;
     *kmax_out = kmax;
+    if (kin_out) *kin_out = kin;
     return ORCA_OK;
 }
 
@@ -496,6 +514,7 @@ namespace {
 int check_adjoint_args(const orca_scene* s, int n_steps, int ckpt_every, void* adj_ws,
                        size_t adj_bytes, const float* vpref_delta) {
     if (!s || n_steps < 0 || ckpt_every < 1) return ORCA_ERR_INVALID_ARG;
+    if (kinematic(&s->params)) return ORCA_ERR_INVALID_ARG;   // not differentiated
     if (vpref_delta && !aligned(vpref_delta, 8)) return ORCA_ERR_INVALID_ARG;
     const AdjLayout L = make_adj_layout((size_t)s->p.n, s->params.max_neighbors, n_steps,
                                         ckpt_every);
@@ -572,7 +591,7 @@ const char* orca_status_string(int status) {
     }
 }
 
-int orca_abi_version(void) { return 2; }
+int orca_abi_version(void) { return 3; }
 
 int orca_workspace_bytes(const orca_params* params, int n_agents, size_t* out_bytes) {
     int st = check_params(params);
@@ -598,7 +617,7 @@ int orca_scene_create(const orca_params* params, const orca_agents* agents, void
     orca_scene* s = new (std::nothrow) orca_scene;
     if (!s) return ORCA_ERR_CAPACITY;
     s->params = *params;
-    init_pipeline(s->p, agents, (int)ncells, kcap_for(params->max_neighbors),
+    init_pipeline(s->p, agents, (int)ncells, kcap_for(params->max_neighbors, kinematic(params)),
                   params->block_size, 0, lay, workspace, params->max_neighbors,
                   params->debug_flags);
     s->p.one = scene_dev(params, 0, s->p.n, 0);
@@ -954,7 +973,8 @@ int orca_batch_create(const orca_params* params, int n_scenes, const int* offset
     if (st != ORCA_OK) return st;
     size_t ncells = 0;
     int kmax = 0;
-    st = check_batch(params, n_scenes, offsets, agents->n_agents, &ncells, &kmax);
+    bool kin = false;
+    st = check_batch(params, n_scenes, offsets, agents->n_agents, &ncells, &kmax, &kin);
     if (st != ORCA_OK) return st;
     const int n = agents->n_agents;
     Layout lay = make_layout((size_t)n, ncells, (size_t)n_scenes);
@@ -972,7 +992,7 @@ int orca_batch_create(const orca_params* params, int n_scenes, const int* offset
     if (!b) return ORCA_ERR_CAPACITY;
     b->n_scenes = n_scenes;
     b->kmax = kmax;
-    init_pipeline(b->p, agents, (int)ncells, kcap_for(kmax), params[0].block_size, n_scenes, lay,
+    init_pipeline(b->p, agents, (int)ncells, kcap_for(kmax, kin), params[0].block_size, n_scenes, lay,
                   workspace, kmax, params[0].debug_flags);
     bool ok = cudaMemset(b->p.buf.err, 0, 16) == cudaSuccess &&
               cudaMemcpy(b->p.buf.scenes, table.data(), table.size() * sizeof(SceneDev),
@@ -1089,7 +1109,8 @@ extern "C" int orca_step_noalloc(const orca_params* params, const orca_agents* a
 
     // a pipeline over the scratch area, held on the host stack
     Pipeline P;
-    init_pipeline(P, agents, (int)ncells, kcap_for(params->max_neighbors), params->block_size,
+    init_pipeline(P, agents, (int)ncells, kcap_for(params->max_neighbors, kinematic(params)),
+                  params->block_size,
                   0, L, w, params->max_neighbors, params->debug_flags);
     P.one = scene_dev(params, 0, n, 0);
     st = prepare(P);

@@ -36,7 +36,14 @@ struct SceneDev {
     int k;
     float inv_tau, inv_dt, dt;
     float f00, f01, f10, f11;
+    // vehicles' kinematic half-planes (off when both flags are false)
+    bool kin_turn, kin_accel;
+    float cos_turn, sin_turn;   // of the largest heading change per step
+    float accel_dt;             // largest forward speed gain per step
 };
+
+// kinematic half-planes a vehicle can add to its LP
+constexpr int kKinLines = 3;
 
 struct OneScene {
     SceneDev s;

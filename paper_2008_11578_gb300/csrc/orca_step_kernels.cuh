@@ -438,14 +438,48 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         }
     }
 
+    // ---- vehicles' kinematic half-planes (off unless the scene sets limits) ----
+    int nlines = cnt;
+    if (ta != 0 && (sc.kin_turn || sc.kin_accel)) {
+        const float sp2 = __fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y));
+        const bool moving = sp2 >= 0.01f;   // |v| >= 0.1 m/s: the heading is defined
+        float hx = 0.0f, hy = 0.0f, sp = 0.0f;
+        if (moving) {
+            sp = sqrtf(sp2);
+            hx = v.x / sp;
+            hy = v.y / sp;
+        } else {
+            const float pl = sqrtf(vpx * vpx + vpy * vpy);
+            if (pl > 0.0f) {
+                hx = vpx / pl;
+                hy = vpy / pl;
+            }
+        }
+        if (moving && sc.kin_turn) {
+            // the heading may turn by at most +-theta: the wedge between the
+            // rays R(+theta) h and R(-theta) h, two half-planes through 0
+            const float lx = sc.cos_turn * hx - sc.sin_turn * hy;
+            const float ly = sc.sin_turn * hx + sc.cos_turn * hy;
+            L[nlines++ * stride] = make_float4(0.0f, 0.0f, -lx, -ly);
+            const float rx = sc.cos_turn * hx + sc.sin_turn * hy;
+            const float ry = -sc.sin_turn * hx + sc.cos_turn * hy;
+            L[nlines++ * stride] = make_float4(0.0f, 0.0f, rx, ry);
+        }
+        if (sc.kin_accel && (hx != 0.0f || hy != 0.0f)) {
+            // forward speed gain at most accel * dt: v . h <= |v| + accel dt
+            const float smax = sp + sc.accel_dt;
+            L[nlines++ * stride] = make_float4(smax * hx, smax * hy, -hy, hx);
+        }
+    }
+
     // ---- velocity LP, least-penetration fallback ----
     float vx, vy, tstar;
     uint32_t act = 0u;
     const int infeasible =
         WORK_UNITS
-            ? solve_velocity_work_units(smem_lines, active ? cnt : 0, vmax, vpx, vpy, vx, vy,
+            ? solve_velocity_work_units(smem_lines, active ? nlines : 0, vmax, vpx, vpy, vx, vy,
                                         tstar, work)
-            : solve_velocity(L, stride, cnt, vmax, vpx, vpy, vx, vy, tstar, work, act);
+            : solve_velocity(L, stride, nlines, vmax, vpx, vpy, vx, vy, tstar, work, act);
     if (!active) return;
     const uint8_t flags = (uint8_t)(infeasible | (any_overlap ? 4 : 0));
 

@@ -42,6 +42,10 @@ class OrcaParams:
     cell_size: float = 2.0
     origin: tuple = (0.0, 0.0)
     extent: tuple = (50.0, 50.0)
+    # kinematic limits of vehicles (rad/s, m/s^2); 0 = off.  The paper's
+    # proposed extension for vehicles (Sec. 5): extra linear constraints
+    vehicle_turn_rate: float = 0.0
+    vehicle_accel: float = 0.0
 
     def grid_dims(self, cell_size: float | None = None) -> tuple[int, int]:
         c = float(self.cell_size if cell_size is None else cell_size)

@@ -566,3 +566,45 @@ def test_arrival_rule_boundaries():
     assert got[:3].tolist() == [True, False, True]
     assert not got[3]                                  # on its first waypoint
     assert oracle.arrived(s, P, np.array([0, 0, 0, 1], np.uint8))[3]
+
+
+def _lone_vehicle(v0, goal, turn_rate=0.0, accel=0.0):
+    P = np.array([[0.0, 0.0]], np.float32)
+    s = scenes.Scene(P, np.array([v0], np.float32), np.array([goal], np.float32),
+                     np.array([1.5], np.float32), np.array([5.0], np.float32),
+                     np.array([1], np.uint8),
+                     scenes.OrcaParams(extent=(100.0, 100.0), origin=(-50.0, -50.0),
+                                       vehicle_turn_rate=turn_rate, vehicle_accel=accel))
+    return oracle.step(s).vel[0]
+
+
+@pytest.mark.parametrize("rate", [0.3, 1.0, 2.5])
+def test_vehicle_turn_limit_closed_form(rate):
+    """A vehicle heading east that wants to go north at full speed turns by
+    exactly theta = rate * dt: v* = 5 sin(theta) (cos theta, sin theta), the
+    projection of v_pref onto the edge of the allowed wedge."""
+    th = float(np.float32(rate)) * 0.25
+    v = _lone_vehicle([3.0, 0.0], [0.0, 40.0], turn_rate=rate)
+    exp = 5.0 * np.sin(th) * np.array([np.cos(th), np.sin(th)])
+    assert np.abs(v - exp).max() <= 1e-9
+
+
+def test_vehicle_accel_limit_closed_form():
+    """Straight ahead at 2 m/s with 2 m/s^2: the next speed is 2 + 2 * 0.25;
+    from rest it is 2 * 0.25 along the preferred velocity."""
+    v = _lone_vehicle([2.0, 0.0], [40.0, 0.0], turn_rate=1.0, accel=2.0)
+    assert np.abs(v - np.array([2.5, 0.0])).max() <= 1e-9
+    v = _lone_vehicle([0.0, 0.0], [30.0, 40.0], turn_rate=1.0, accel=2.0)
+    assert np.abs(v - 0.5 * np.array([0.6, 0.8])).max() <= 1e-9
+    # limits off: the unconstrained preferred velocity
+    v = _lone_vehicle([2.0, 0.0], [0.0, 40.0])
+    assert np.abs(v - np.array([0.0, 5.0])).max() <= 1e-9
+
+
+def test_kinematic_limits_leave_pedestrians_alone():
+    s = scenes.open_square(300, 20.0, seed=7)
+    s.params.vehicle_turn_rate, s.params.vehicle_accel = 0.5, 1.0
+    a = oracle.step(s)
+    s.params.vehicle_turn_rate, s.params.vehicle_accel = 0.0, 0.0
+    b = oracle.step(s)
+    assert np.array_equal(a.vel, b.vel)

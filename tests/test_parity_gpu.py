@@ -243,3 +243,32 @@ def test_work_unit_lp_matches_per_thread_lp(name):
     assert np.abs(a[0].astype(np.float64) - b[0]).max() <= 1e-5
     g = gpu_step(s, flags=api.LP_WORK_UNITS)
     compare(s, g, sel=np.arange(0, s.n, max(1, s.n // 3000)))
+
+
+@pytest.mark.parametrize("which", ["shared_space", "waypoints", "clusters"])
+def test_vehicle_kinematic_limits(which):
+    """Vehicles with turn-rate and acceleration limits (extra half-planes)
+    against the oracle, per step along a short GPU rollout."""
+    s = {"shared_space": lambda: scenes.shared_space(n_ped=6400, n_veh=300, side=160.0, seed=8),
+         "waypoints": lambda: scenes.waypoint_square(n_ped=1500, n_veh=60, side=70.0, seed=9),
+         "clusters": lambda: scenes.clusters(n=62500, side=500.0, n_clusters_axis=2,
+                                             vehicle_every=20)}[which]()
+    s.params.vehicle_turn_rate, s.params.vehicle_accel = 0.8, 2.0
+    sel = None if s.n < 20000 else np.arange(0, s.n, 7)
+    veh = s.type == 1
+    for t in range(4):
+        g = gpu_step(s)
+        compare(s, g, sel=sel)
+        if t == 0 and s.route is None:
+            # from rest the speed along the preferred direction grows by at most
+            # accel * dt = 0.5 m/s for vehicles whose LP is feasible (an empty LP
+            # trades the limit against the ORCA half-planes); it binds somewhere
+            ok = veh & ((g["flags"] & 1) == 0)
+            h = (s.goal - s.pos)[ok].astype(np.float64)
+            h /= np.linalg.norm(h, axis=1, keepdims=True)
+            along = (g["vel"][ok].astype(np.float64) * h).sum(1)
+            assert ok.sum() >= 1 and along.max() <= 0.5 + 1e-5
+            assert (along > 0.5 - 1e-5).sum() >= 1
+        s.pos, s.vel = g["pos"], g["vel"]
+        if "wp_idx" in g:
+            s.wp_idx = g["wp_idx"]
