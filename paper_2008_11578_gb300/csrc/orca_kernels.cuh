@@ -53,7 +53,7 @@ struct OneScene {
 struct ManyScenes {
     const SceneDev* __restrict__ s;
     const int* __restrict__ sid;   // scene of every sorted slot (fixed)
-    __device__ __forceinline__ SceneDev get(int i) const { return s[__ldg(sid + i)]; }
+    __device__ __forceinline__ const SceneDev& get(int i) const { return s[__ldg(sid + i)]; }
 };
 
 // caller-order per-agent inputs of the solve kernel

@@ -38,7 +38,7 @@ __global__ void bin_count_kernel(int n, SRC src, const float2* __restrict__ pos,
                                  uint32_t* __restrict__ count) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const SceneDev sc = src.get(i);
+    const SceneDev& sc = src.get(i);
     float2 p = pos[i];
     int cx = cell_axis(p.x, sc.origin_x, sc.inv_cell, sc.nx);
     int cy = cell_axis(p.y, sc.origin_y, sc.inv_cell, sc.ny);
@@ -290,7 +290,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     if (!WORK_UNITS && s_raw >= n) return;
     const bool active = s_raw < n;
     const int s = active ? s_raw : n - 1;
-    const SceneDev sc = src.get(s);
+    const SceneDev& sc = src.get(s);
     const float2 p = pos[s];
     const float2 v = vel[s];
     const uint2 as = aux[s];
@@ -315,6 +315,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     if (k > 0) {
         const int nx = sc.nx, ny = sc.ny;
         const int mmax = max(max(cx, nx - 1 - cx), max(cy, ny - 1 - cy));
+        const float prx = __fsub_rn(p.x, sc.origin_x), pry = __fsub_rn(p.y, sc.origin_y);
         for (int m = 0; m <= mmax; ++m) {
             // ring m = row cy-m, row cy+m (each one contiguous run of cells)
             // and the two side cells of every row strictly between them
@@ -323,19 +324,36 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
             const int ya = max(ylo + 1, 0), yb = min(yhi - 1, ny - 1);
             const int nr = (m == 0) ? 1 : 2 + 2 * max(0, yb - ya + 1);
             for (int rr = 0; rr < nr; ++rr) {
-                int c0, c1;
+                int ry, rx0, rx1;
                 if (rr < 2) {
-                    const int y = rr ? yhi : ylo;
-                    if (y < 0 || y >= ny) continue;
-                    c0 = y * nx + x0;
-                    c1 = y * nx + x1;
+                    ry = rr ? yhi : ylo;
+                    if (ry < 0 || ry >= ny) continue;
+                    rx0 = x0;
+                    rx1 = x1;
                 } else {
                     const int q = rr - 2;
-                    const int y = ya + (q >> 1);
-                    const int x = (q & 1) ? cx + m : cx - m;
-                    if (x < 0 || x >= nx) continue;
-                    c0 = c1 = y * nx + x;
+                    ry = ya + (q >> 1);
+                    rx0 = rx1 = (q & 1) ? cx + m : cx - m;
+                    if (rx0 < 0 || rx0 >= nx) continue;
                 }
+                if (m > 0) {
+                    // No agent of cells rx0..rx1 of row ry can enter the list
+                    // when the run's box is beyond the k-th key (or R_n).  The
+                    // box is taken relative to the grid origin, like the cell
+                    // assignment, widened by the same cell-rounding margin as
+                    // the ring bound, and unbounded toward the grid edge (agents
+                    // outside the box are clamped into edge cells).
+                    const float cz = sc.cell_size, mg = sc.ring_delta * cz;
+                    const float bx0 = rx0 == 0 ? -CUDART_INF_F : (float)rx0 * cz - mg;
+                    const float bx1 = rx1 == nx - 1 ? CUDART_INF_F : (float)(rx1 + 1) * cz + mg;
+                    const float by0 = ry == 0 ? -CUDART_INF_F : (float)ry * cz - mg;
+                    const float by1 = ry == ny - 1 ? CUDART_INF_F : (float)(ry + 1) * cz + mg;
+                    const float ex = fmaxf(fmaxf(bx0 - prx, prx - bx1), 0.0f);
+                    const float ey = fmaxf(fmaxf(by0 - pry, pry - by1), 0.0f);
+                    const float bd2 = (ex * ex + ey * ey) * 0.99999f;
+                    if (bd2 >= R2 || (cnt >= k && bd2 > thr_d)) continue;
+                }
+                const int c0 = ry * nx + rx0, c1 = ry * nx + rx1;
                 const int jb = (int)__ldg(cs + c0), je = (int)__ldg(cs + c1 + 1);
                 n_cand += je - jb;
                 for (int j = jb; j < je; ++j) {
