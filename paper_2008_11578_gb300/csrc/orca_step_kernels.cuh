@@ -306,7 +306,9 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     // An admitted candidate shifts only the entries behind it.
     const int k = sc.k;
     float thr_d = CUDART_INF_F;   // key of the k-th entry once the list is full
-    int thr_o = INT_MAX;
+    // (d^2, original index) as one 64-bit key: d^2 >= 0, so its bits order
+    // like the value, and the index breaks ties in the low word
+    unsigned long long thr_key = ~0ull;
     int cnt = 0;
     int n_cand = 0, work = 0;
     const float R2 = sc.R2;
@@ -361,11 +363,15 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                     const float d2 = key_d2(p.x, p.y, q.x, q.y);
                     if (d2 < R2 && d2 <= thr_d && j != s) {
                         const int oj = aux_orig(__ldg(aux + j));
-                        if (d2 < thr_d || oj < thr_o) {
-                            int at = min(cnt, k - 1);   // a full list drops its last entry
+                        const unsigned long long key =
+                            ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)oj;
+                        if (key < thr_key) {
+                            int at = min(cnt, k - 1);
                             while (at > 0) {
                                 const float4 e = L[(at - 1) * stride];
-                                if (e.x < d2 || (e.x == d2 && __float_as_int(e.z) < oj)) break;
+                                const unsigned long long ek =
+                                    ((unsigned long long)__float_as_uint(e.x) << 32) | __float_as_uint(e.z);
+                                if (ek < key) break;
                                 L[at * stride] = e;
                                 --at;
                             }
@@ -375,7 +381,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                             if (cnt == k) {
                                 const float4 e = L[(k - 1) * stride];
                                 thr_d = e.x;
-                                thr_o = __float_as_int(e.z);
+                                thr_key = ((unsigned long long)__float_as_uint(e.x) << 32) | __float_as_uint(e.z);
                             }
                         }
                     }
