@@ -178,6 +178,22 @@ def _dist():
     return world, rank, local
 
 
+def replica_throughput(local_seconds, units, world, device=None):
+    """Whole-job throughput of `world` independent replicas.
+
+    Each rank processed `units` units in `local_seconds`; the job takes as long
+    as its slowest rank, so the rate is world * units / max over ranks.
+    Returns (rate, slowest seconds).  Collective only when world > 1.
+    """
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    slowest = float(t.item())
+    return units * world / slowest, slowest
+
+
 def run_reference(args):
     """The FP64 CPU oracle on this host's cores, bounded sample per step."""
     world, rank, _ = _dist()
@@ -447,11 +463,7 @@ def run_ours(args):
     solve_ms = [api.event_elapsed_ms(a, b) for a, b in sv]
     bin_ms = [api.event_elapsed_ms(a, b) for a, b in bv]
     total_s = sum(step_ms) / 1e3
-    t = torch.tensor([total_s], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_max = float(t.item())
-    value = n * args.steps * world / total_max
+    value, total_max = replica_throughput(total_s, n * args.steps, world, dev)
     clocks = clk.summary()
 
     # ---- algorithmic FLOPs of the solve kernel (untimed counting step) ----
@@ -512,10 +524,8 @@ def run_ours(args):
             eev[k][1].record(stream)
         barrier()
         e_total = sum(a.elapsed_time(b) for a, b in eev) / 1e3
-        te = torch.tensor([e_total], device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": n * args.steps * world / float(te.item()), "unit": METRIC,
+        e2e = {"value": replica_throughput(e_total, n * args.steps, world, dev)[0],
+               "unit": METRIC,
                "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 2 * 8 * n}
 
     status = ds.sync_status()
