@@ -44,13 +44,14 @@ METRIC = "agent-steps/s"
 #   per agent: preferred velocity 10, disc clip 6, integration 4,
 #     1D set-ups amortised 10                                       = 30
 FLOPS_CAND, FLOPS_LINE, FLOPS_PAIR, FLOPS_AGENT = 5, 50, 10, 30
-# Algorithmic DRAM bytes of the binning phase:
-#   bin_count: position 8 read, key + slot 8 written, cell counter 8 (atomic
-#     read-modify-write)                                            = 24 / agent
-#   scatter: key, slot, cell start 12 + state 25 read, state 25 written = 62 / agent
-#   scan: count read 4, count cleared 4, start written 4; add pass start
-#     read + written 8                                              = 20 / cell
-BIN_BYTES_AGENT, BIN_BYTES_CELL = 24 + 62, 20
+# Algorithmic DRAM bytes of the binning kernel on the first step of a call
+# (the bench times one-step calls, so every timed step is a first step):
+#   cell keys: caller position 8 read, key + slot 8 written, cell counter 8
+#     (atomic read-modify-write)                                     = 24 / agent
+#   scatter: key + slot 8, cell start 4, caller state (position 8, velocity
+#     8, radius 4, type 1) 21 read, sorted state 24 written           = 57 / agent
+#   scan: count read 4, count cleared 4, start written 4              = 12 / cell
+BIN_BYTES_AGENT, BIN_BYTES_CELL = 24 + 57, 12
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -310,6 +311,8 @@ def measure_batched(dev, flush, n_steps=50, tune=True):
     loop_ms = p0.elapsed_time(p1)
     same = all(torch.equal(ds.pos, b.pos[b.scene_slice(i)]) and
                torch.equal(ds.vel, b.vel[b.scene_slice(i)]) for i, ds in enumerate(plain))
+    graph_launches = b.launch_count(n_steps)
+    loop_launches = sum(ds.launch_count(n_steps) for ds in plain)
     for ds in plain:
         ds.close()
     b.close()
@@ -318,7 +321,7 @@ def measure_batched(dev, flush, n_steps=50, tune=True):
             "plain_loop_value": total * n_steps / (loop_ms / 1e3), "unit": METRIC,
             "graph_ms": graph_ms, "plain_loop_ms": loop_ms,
             "speedup_vs_plain_loop": loop_ms / graph_ms, "bitwise_equal": bool(same),
-            "graph_launches": 2 + 5 * n_steps, "plain_loop_launches": len(sl) * (2 + 5 * n_steps),
+            "graph_launches": graph_launches, "plain_loop_launches": loop_launches,
             "status": status,
             "autotune": None if tuned is None else
             {"alpha": tuned.alpha, "block_size": tuned.block_size,
@@ -489,16 +492,16 @@ def run_ours(args):
                                      "lp_pairs": c[2] / n, "fallback_frac": c[3] / n},
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz (nominal max clock)"}
 
-    # ---- binning phase (bin_count, 3-phase scan, scatter): HBM bound ----
+    # ---- binning phase (one cooperative kernel): HBM bound ----
     ncells = int(ds.params.grid_nx) * int(ds.params.grid_ny)
     bin_bytes = BIN_BYTES_AGENT * n + BIN_BYTES_CELL * ncells
     bin_s = statistics.mean(bin_ms) / 1e3
     hbm = float(_peaks().get("hbm_gbs", 6681.5))
     roofline_binning = {"bound": "hbm", "achieved": bin_bytes / bin_s / 1e9, "peak": hbm,
                         "unit": "GB/s", "frac": bin_bytes / bin_s / 1e9 / hbm, "traffic": None,
-                        "kernels": "bin_count + scan_blocks + scan_bsum + scan_add + scatter",
+                        "kernels": "bin_kernel (cooperative: cell keys, scan, scatter)",
                         "ms": statistics.mean(bin_ms), "bytes_per_step": bin_bytes,
-                        "cells": ncells, "launches_per_step": 5,
+                        "cells": ncells, "launches_per_step": 1,
                         "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)"}
 
     # ---- end to end through the public API from pinned host buffers ----

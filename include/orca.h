@@ -63,8 +63,13 @@ extern "C" {
 /* Solve the 2D LPs with the batch-LP load balancing the paper uses (Sec. 3,
    LP paragraphs: re-solves split into work units that every thread of a
    block shares) instead of one thread per LP.  Results agree to FP32
-   rounding.  Other bits are rejected. */
+   rounding. */
 #define ORCA_FLAG_LP_WORK_UNITS 2u
+/* Test hook for failure detection: the first block of every binning kernel
+   leaves without arriving at the grid barrier, so the other blocks' bounded
+   waits run out.  The step then reports ORCA_ERR_TIMEOUT through
+   orca_scene_sync_status() and leaves the caller's arrays untouched. */
+#define ORCA_DEBUG_BARRIER_TIMEOUT 4u
 
 /*
  * Global parameters of one scene (Sec. 3 and 3.1).
@@ -80,7 +85,8 @@ extern "C" {
  *                   changes
  *   origin_x/y, grid_nx/ny   grid box; agents outside clamp to edge cells
  *   block_size      threads per block of the solve kernel (0 = 128)
- *   debug_flags     ORCA_DEBUG_NONE or ORCA_FLAG_LP_WORK_UNITS
+ *   debug_flags     ORCA_DEBUG_NONE, or ORCA_FLAG_LP_WORK_UNITS and/or
+ *                   ORCA_DEBUG_BARRIER_TIMEOUT
  *   vehicle_turn_rate, vehicle_accel   kinematic limits of vehicles (type 1),
  *                   rad/s and m/s^2, 0 = off (default).  The paper names such
  *                   extra linear constraints as its extension for vehicles
@@ -158,7 +164,8 @@ int orca_workspace_bytes(const orca_params *params, int n_agents, size_t *out_by
 /*
  * Create a scene over caller-owned agent arrays and workspace.  Validates
  * everything that can be checked on the host (sizes, alignment, parameter
- * ranges) and launches nothing.  *out receives a host object that
+ * ranges), clears the workspace's error word and cell counts (synchronous
+ * memsets) and launches no kernel.  *out receives a host object that
  * orca_scene_destroy() frees.
  */
 int orca_scene_create(const orca_params *params, const orca_agents *agents,
@@ -195,8 +202,9 @@ int orca_scene_set_solve_events(orca_scene *scene, void *begin, void *end);
 
 /*
  * The same for the binning phase (cell keys, the scan of the cell counts and
- * the scatter into cell order): begin is recorded before the bin_count
- * kernel and end after the scatter kernel of every following step.
+ * the scatter into cell order, one cooperative kernel per step): begin and
+ * end bracket that kernel.  On the first step of a call it also reads the
+ * caller's arrays (later steps read the state the solve kernel wrote).
  */
 int orca_scene_set_bin_events(orca_scene *scene, void *begin, void *end);
 
@@ -232,6 +240,11 @@ int orca_scene_graph_launch(orca_scene *scene, void *stream);
 /*
  * Synchronise the device, then read and clear the scene's device error
  * word.  Returns ORCA_OK or the first recorded error status.
+ * ORCA_ERR_TIMEOUT: a grid barrier of the binning kernel waited longer than
+ * about half a second, or a later step found the cell counts such a step
+ * left behind (or two calls ran on one scene at once); the results of those
+ * steps are invalid.  This call also resets the barrier and the cell counts,
+ * so the scene can step again.
  */
 int orca_scene_sync_status(orca_scene *scene);
 

@@ -34,6 +34,7 @@ def _stream_handle(stream):
 
 
 LP_WORK_UNITS = 2   # orca_params.debug_flags: the paper's work-unit batch LP
+BARRIER_TIMEOUT_TEST = 4   # orca_params.debug_flags: failure-detection test hook
 
 
 def make_params(p, cell_size: float | None = None, block_size: int = 0,
@@ -104,7 +105,7 @@ def orca_scene_set_solve_events(handle, begin=None, end=None):
 
 
 def orca_scene_set_bin_events(handle, begin=None, end=None):
-    """Bracket the binning phase (bin_count .. scatter) of every following
+    """Bracket the binning kernel (cell keys, scan, scatter) of every following
     step with two torch CUDA events (or None to stop)."""
     for ev in (begin, end):
         if ev is not None and ev.cuda_event == 0:

@@ -260,7 +260,9 @@ adjoint_kernel(int n, SceneDev sc, const float2* __restrict__ pos, const float2*
                const float2* __restrict__ vbar_next, const float2* __restrict__ dl_dv,
                float2* __restrict__ pbar_cur, float2* __restrict__ vbar_cur,
                float2* __restrict__ pbar_spare, float2* __restrict__ vbar_spare,
-               float2* __restrict__ dvpd, float2* __restrict__ dwp) {
+               float2* __restrict__ dvpd, float2* __restrict__ dwp, const int* __restrict__ err) {
+    // the replayed records are not valid after a binning error (see solve_kernel)
+    if (__ldcg(err) & (ERR_BIT_TIMEOUT | ERR_BIT_STATE)) return;
     const int A = blockIdx.x * blockDim.x + threadIdx.x;
     if (A >= n) return;
     pbar_spare[A] = make_float2(0.0f, 0.0f);

@@ -43,8 +43,10 @@ struct Layout {
 
 Layout make_layout(size_t n, size_t ncells, size_t n_scenes) {
     Layout L{};
-    // block sums of the cell scan, and of the agent scan of orca_scene_remove_arrived
-    size_t nb = (std::max(ncells, n) + kScanChunk - 1) / kScanChunk;
+    // block sums of the binning kernel's scan (one per launch block), and of
+    // the agent scan of orca_scene_remove_arrived
+    size_t nb = std::max((std::max(ncells, n) + kScanChunk - 1) / kScanChunk,
+                         (size_t)kBinGridMax);
     size_t o = 0;
     auto take = [&](size_t bytes) {
         size_t at = o;
@@ -120,7 +122,8 @@ int check_params(const orca_params* p) {
         return ORCA_ERR_CAPACITY;
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 128 || p->block_size % 32))
         return ORCA_ERR_INVALID_ARG;
-    if (p->debug_flags & ~(unsigned)ORCA_FLAG_LP_WORK_UNITS) return ORCA_ERR_INVALID_ARG;
+    if (p->debug_flags & ~(unsigned)(ORCA_FLAG_LP_WORK_UNITS | ORCA_DEBUG_BARRIER_TIMEOUT))
+        return ORCA_ERR_INVALID_ARG;
     if (!std::isfinite(p->vehicle_turn_rate) || !std::isfinite(p->vehicle_accel) ||
         p->vehicle_turn_rate < 0.0f || p->vehicle_accel < 0.0f ||
         (double)p->vehicle_turn_rate * (double)p->dt >= 1.5707963267948966)
@@ -219,10 +222,10 @@ template <class SRC>
 void launch_solve(int mode, int grid, int block, size_t smem, cudaStream_t st, int n, SRC src,
                   const float2* pos, const float2* vel, const uint2* aux, const uint32_t* start,
                   AgentIn ain, const float2* vpd, StepOut out, DebugOut dbg,
-                  unsigned long long* counters) {
+                  unsigned long long* counters, const int* err) {
 #define ORCA_SOLVE(M, W)                                                                    \
     solve_kernel<SRC, M, W><<<grid, block, smem, st>>>(n, src, pos, vel, aux, start, ain, vpd, \
-                                                        out, dbg, counters)
+                                                        out, dbg, counters, err)
     if (mode == MODE_COUNT) ORCA_SOLVE(MODE_COUNT, false);
     else if (mode == MODE_RECORD) ORCA_SOLVE(MODE_RECORD, false);
     else if (mode == MODE_WORK_UNITS) ORCA_SOLVE(MODE_PLAIN, true);
@@ -237,7 +240,6 @@ struct Pipeline {
     orca_agents agents;
     int n;
     int ncells;
-    int nblocks;
     int kcap;
     int block;
     int n_scenes;
@@ -254,6 +256,7 @@ struct Pipeline {
     unsigned long long* counters;
     cudaGraphExec_t graph;
     int graph_steps;
+    int bin_grid_max;   // co-resident blocks of the binning kernel on this device
 };
 
 size_t solve_smem(const Pipeline& P) { return (size_t)P.kcap * P.block * sizeof(float4); }
@@ -270,7 +273,34 @@ int step_mode(const Pipeline& P) {
     return (P.flags & ORCA_FLAG_LP_WORK_UNITS) ? MODE_WORK_UNITS : MODE_PLAIN;
 }
 
-// Enqueue the load and n_steps steps.  dbg_for(t) gives the solve
+// The binning kernel of one step (cooperative launch, grid sized to what is
+// resident at once on this device).  first: from the caller's arrays.
+template <class SRC>
+void launch_bin(const Pipeline& P, SRC src, bool first, int cur, cudaStream_t st) {
+    const Buffers& B = P.buf;
+    const orca_agents& A = P.agents;
+    const BinArgs a{P.n, P.ncells, (const float2*)A.pos, (const float2*)A.vel, A.radius, A.type,
+                    B.pos0, B.vel0, B.aux[cur], B.key, B.slot, B.count, B.start, B.bsum,
+                    B.pos1, B.vel1, B.aux[1 - cur], B.err,
+                    (P.flags & ORCA_DEBUG_BARRIER_TIMEOUT) ? 1 : 0};
+    const long long work = std::max((long long)P.n, (long long)P.ncells / 4);
+    const int grid = (int)std::max(
+        1LL, std::min((long long)P.bin_grid_max, (work + kBinThreads - 1) / kBinThreads));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kBinThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (first) cudaLaunchKernelEx(&cfg, bin_kernel<SRC, true>, src, a);
+    else cudaLaunchKernelEx(&cfg, bin_kernel<SRC, false>, src, a);
+}
+
+// Enqueue n_steps steps.  dbg_for(t) gives the solve
 // kernel's optional outputs of step t.
 template <class SRC, class DBG>
 void enqueue_steps(const Pipeline& P, SRC src, int n_steps, const float* vpref_delta,
@@ -278,15 +308,6 @@ void enqueue_steps(const Pipeline& P, SRC src, int n_steps, const float* vpref_d
     const int n = P.n;
     const Buffers& B = P.buf;
     const orca_agents& A = P.agents;
-    const int tb = 256;
-    const int gb = (n + tb - 1) / tb;
-    {
-        int g = (std::max(n, P.ncells) + tb - 1) / tb;
-        g = std::min(g, 152 * 16);
-        load_kernel<<<g, tb, 0, st>>>(n, (const float2*)A.pos, (const float2*)A.vel, A.radius,
-                                      A.type, B.pos0, B.vel0, B.aux[0], B.count, P.ncells,
-                                      B.err);
-    }
     AgentIn ain{(const float2*)A.goal, A.max_speed, A.route, (const float2*)A.waypoints,
                 A.n_waypoints, A.wp_idx};
     int cur = 0;
@@ -295,15 +316,9 @@ void enqueue_steps(const Pipeline& P, SRC src, int n_steps, const float* vpref_d
     const size_t smem = solve_smem(P);
     for (int t = 0; t < n_steps; ++t) {
         if (P.bin_begin) cudaEventRecord(P.bin_begin, st);
-        // later steps were binned by the previous step's solve kernel
-        if (t == 0) bin_count_kernel<SRC><<<gb, tb, 0, st>>>(n, src, B.pos0, B.key, B.slot, B.count);
-        scan_blocks_kernel<<<P.nblocks, kScanThreads, 0, st>>>(B.count, B.start, B.bsum,
-                                                               P.ncells);
-        scan_bsum_kernel<<<1, 1024, 0, st>>>(B.bsum, P.nblocks);
-        scan_add_kernel<<<(P.ncells / 4 + 256) / 256, 256, 0, st>>>(B.start, B.bsum, P.ncells,
-                                                                    P.nblocks);
-        scatter_kernel<<<gb, tb, 0, st>>>(n, B.key, B.slot, B.start, B.pos0, B.vel0,
-                                          B.aux[cur], B.pos1, B.vel1, B.aux[1 - cur]);
+        // step 0 bins the caller's state; later steps were binned by the
+        // previous step's solve kernel
+        launch_bin(P, src, t == 0, cur, st);
         cur = 1 - cur;
         if (P.bin_end) cudaEventRecord(P.bin_end, st);
         const float2* vpd =
@@ -314,7 +329,7 @@ void enqueue_steps(const Pipeline& P, SRC src, int n_steps, const float* vpref_d
                                            nullptr}
                                  : StepOut{B.pos0, B.vel0, false, B.key, B.slot, B.count};
         launch_solve(mode, sgrid, sb, smem, st, n, src, B.pos1, B.vel1, B.aux[cur], B.start,
-                     ain, vpd, out, dbg_for(t), P.counters);
+                     ain, vpd, out, dbg_for(t), P.counters, B.err);
         if (P.ev_end) cudaEventRecord(P.ev_end, st);
     }
 }
@@ -329,10 +344,29 @@ int run_steps(const Pipeline& P, int n_steps, const float* vpref_delta, cudaStre
     return cuda_status(cudaGetLastError());
 }
 
-int prepare(const Pipeline& P) {
+// Blocks of the binning kernel that are resident at once on the current
+// device (both variants), at most kBinGridMax.
+template <class SRC>
+cudaError_t bin_grid_max(int* out) {
+    int dev = 0, sms = 0, b0 = 0, b1 = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, bin_kernel<SRC, false>, kBinThreads, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, bin_kernel<SRC, true>, kBinThreads, 0);
+    if (e == cudaSuccess && std::min(b0, b1) < 1) e = cudaErrorInvalidConfiguration;
+    *out = std::max(1, std::min(kBinGridMax, std::min(b0, b1) * sms));
+    return e;
+}
+
+int prepare(Pipeline& P) {
     const size_t smem = solve_smem(P);
     cudaError_t e = P.n_scenes == 0 ? prepare_solve<OneScene>(smem)
                                     : prepare_solve<ManyScenes>(smem);
+    if (e == cudaSuccess)
+        e = P.n_scenes == 0 ? bin_grid_max<OneScene>(&P.bin_grid_max)
+                            : bin_grid_max<ManyScenes>(&P.bin_grid_max);
     return cuda_status(e);
 }
 
@@ -340,16 +374,21 @@ int read_status(const Pipeline& P) {
     if (cudaDeviceSynchronize() != cudaSuccess) return ORCA_ERR_CUDA;
     int h[4] = {0, 0, 0, 0};
     if (cudaMemcpy(h, P.buf.err, 16, cudaMemcpyDeviceToHost) != cudaSuccess) return ORCA_ERR_CUDA;
+    // clears the status bits and the binning kernel's barrier words; after a
+    // barrier gave up, the cell counts may be left mid-step, so clear them too
     if (cudaMemset(P.buf.err, 0, 16) != cudaSuccess) return ORCA_ERR_CUDA;
+    if ((h[0] & (ERR_BIT_TIMEOUT | ERR_BIT_STATE)) &&
+        cudaMemset(P.buf.count, 0, (size_t)P.ncells * 4) != cudaSuccess)
+        return ORCA_ERR_CUDA;
     if (h[0] & ERR_BIT_NONFINITE) return ORCA_ERR_NONFINITE;
-    if (h[0] & ERR_BIT_TIMEOUT) return ORCA_ERR_TIMEOUT;
+    if (h[0] & (ERR_BIT_TIMEOUT | ERR_BIT_STATE)) return ORCA_ERR_TIMEOUT;
     return ORCA_OK;
 }
 
 int launch_count(const Pipeline& P, int n_steps) {
     if (n_steps < 0) return -1;
     if (P.n == 0 || n_steps == 0) return 0;
-    return 2 + 5 * n_steps;   // load + bin_count, then 3 scans + scatter + solve per step
+    return 2 * n_steps;   // binning + solve per step
 }
 
 void drop_graph(Pipeline& P) {
@@ -409,7 +448,6 @@ void init_pipeline(Pipeline& P, const orca_agents* agents, int ncells, int kcap,
     P.flags = flags;
     P.n = agents->n_agents;
     P.ncells = ncells;
-    P.nblocks = (ncells + kScanChunk - 1) / kScanChunk;
     P.kcap = kcap;
     P.block = block ? block : 128;
     P.n_scenes = n_scenes;
@@ -424,6 +462,7 @@ void init_pipeline(Pipeline& P, const orca_agents* agents, int ncells, int kcap,
     P.counters = nullptr;
     P.graph = nullptr;
     P.graph_steps = 0;
+    P.bin_grid_max = 1;
 }
 
 // Host-side checks of a batch description; fills the total cell count and
@@ -624,7 +663,9 @@ int orca_scene_create(const orca_params* params, const orca_agents* agents, void
     s->adj_steps = -1;
     s->adj_every = 0;
     s->adj_ws = nullptr;
-    if (cudaMemset(s->p.buf.err, 0, 16) != cudaSuccess || prepare(s->p) != ORCA_OK) {
+    // the binning kernel expects zero cell counts on entry
+    if (cudaMemset(s->p.buf.err, 0, 16) != cudaSuccess ||
+        cudaMemset(s->p.buf.count, 0, ncells * 4) != cudaSuccess || prepare(s->p) != ORCA_OK) {
         delete s;
         return ORCA_ERR_CUDA;
     }
@@ -865,7 +906,7 @@ int orca_adjoint(orca_scene* s, int n_steps, int ckpt_every, const float* vpref_
                 bp[nx], bv[nx], dl_dvel_traj ? (const float2*)dl_dvel_traj + tn : nullptr,
                 bp[cu], bv[cu], bp[sp], bv[sp],
                 dl_dvpref_delta ? (float2*)dl_dvpref_delta + tn : nullptr,
-                (float2*)dl_dwaypoints);
+                (float2*)dl_dwaypoints, s->p.buf.err);
             const int old_nx = nx;
             nx = cu;
             cu = sp;
@@ -936,7 +977,7 @@ int orca_step_vjp(orca_scene* s, void* adj_ws, size_t adj_bytes, const float* po
         n, s->p.one, rec.r_pos, rec.r_vel, A.radius, A.type, rec.r_nbr, rec.k, rec.r_act,
         rec.r_wp, rec.r_vnew, ain, (const float2*)vpref_delta, (const float2*)dl_dpos_next,
         (const float2*)dl_dvel_next, nullptr, bp[1], bv[1], bp[2], bv[2],
-        (float2*)dl_dvpref_delta, (float2*)dl_dwaypoints);
+        (float2*)dl_dvpref_delta, (float2*)dl_dwaypoints, s->p.buf.err);
     ok = cudaMemcpyAsync(dl_dpos, bp[1], nb, cudaMemcpyDeviceToDevice, stm) == cudaSuccess &&
          cudaMemcpyAsync(dl_dvel, bv[1], nb, cudaMemcpyDeviceToDevice, stm) == cudaSuccess;
     if (!ok) return ORCA_ERR_CUDA;
@@ -946,8 +987,7 @@ int orca_step_vjp(orca_scene* s, void* adj_ws, size_t adj_bytes, const float* po
 int orca_adjoint_launch_count(const orca_scene* s, int n_steps, int ckpt_every) {
     if (!s || n_steps < 0 || ckpt_every < 1) return -1;
     if (s->p.n == 0 || n_steps == 0) return 0;
-    const int n_ck = (n_steps + ckpt_every - 1) / ckpt_every;
-    return n_ck * 2 + 5 * n_steps + n_steps;   // replays (load + bin_count + steps) + adjoint kernels
+    return 2 * n_steps + n_steps;   // replayed steps (binning + solve) + adjoint kernels
 }
 
 // ------------------------------------------------------------- batches ----
@@ -995,6 +1035,7 @@ int orca_batch_create(const orca_params* params, int n_scenes, const int* offset
     init_pipeline(b->p, agents, (int)ncells, kcap_for(kmax, kin), params[0].block_size, n_scenes, lay,
                   workspace, kmax, params[0].debug_flags);
     bool ok = cudaMemset(b->p.buf.err, 0, 16) == cudaSuccess &&
+              cudaMemset(b->p.buf.count, 0, (size_t)ncells * 4) == cudaSuccess &&
               cudaMemcpy(b->p.buf.scenes, table.data(), table.size() * sizeof(SceneDev),
                          cudaMemcpyHostToDevice) == cudaSuccess &&
               (n == 0 || cudaMemcpy(b->p.buf.sid, sid.data(), sid.size() * sizeof(int32_t),
@@ -1115,9 +1156,10 @@ extern "C" int orca_step_noalloc(const orca_params* params, const orca_agents* a
     P.one = scene_dev(params, 0, n, 0);
     st = prepare(P);
     if (st != ORCA_OK) return st;
-    // the error word and the cell counts must start at zero; the load
-    // kernel clears the counts, the error word is cleared here
-    if (cudaMemsetAsync(P.buf.err, 0, 16, stm) != cudaSuccess) return ORCA_ERR_CUDA;
+    // the error word, the barrier words and the cell counts start at zero
+    if (cudaMemsetAsync(P.buf.err, 0, 16, stm) != cudaSuccess ||
+        cudaMemsetAsync(P.buf.count, 0, ncells * 4, stm) != cudaSuccess)
+        return ORCA_ERR_CUDA;
     st = run_steps(P, n_steps, vpref_delta, stm);
     if (st != ORCA_OK) return st;
     if (synchronize) {
@@ -1126,7 +1168,7 @@ extern "C" int orca_step_noalloc(const orca_params* params, const orca_agents* a
         if (cudaMemcpy(h, P.buf.err, 16, cudaMemcpyDeviceToHost) != cudaSuccess)
             return ORCA_ERR_CUDA;
         if (h[0] & ERR_BIT_NONFINITE) return ORCA_ERR_NONFINITE;
-        if (h[0] & ERR_BIT_TIMEOUT) return ORCA_ERR_TIMEOUT;
+        if (h[0] & (ERR_BIT_TIMEOUT | ERR_BIT_STATE)) return ORCA_ERR_TIMEOUT;
     }
     return ORCA_OK;
 }

@@ -123,7 +123,10 @@ constexpr int MODE_WORK_UNITS = 3;
 // [3] agents that took the least-penetration fallback, [4] agents.
 constexpr int kNumCounters = 5;
 
-enum : int { ERR_BIT_NONFINITE = 1, ERR_BIT_TIMEOUT = 2 };
+// Device error word bits.  ERR_BIT_STATE: the binning kernel found cell
+// counts that do not sum to the agent count (reported as a timeout: the only
+// in-library cause is a step cut short by a barrier that gave up).
+enum : int { ERR_BIT_NONFINITE = 1, ERR_BIT_TIMEOUT = 2, ERR_BIT_STATE = 4 };
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;

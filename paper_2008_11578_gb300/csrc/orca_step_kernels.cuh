@@ -1,7 +1,7 @@
 // orca_step_kernels.cuh -- device kernels of the ORCA step (sm_103a).
 //
-// Memory-bound kernels (load, bin_count, scan, scatter) are one
-// thread per element with coalesced accesses; the solve kernel is one thread
+// The binning kernel is one cooperative launch per step (counting sort by
+// cell in four phases); the solve kernel is one thread
 // per agent in cell-sorted order, so the 32 agents of a warp come from a few
 // neighbouring cells and read the same candidate cells through L1.
 #pragma once
@@ -9,43 +9,6 @@
 #include "orca_kernels.cuh"
 
 namespace orca {
-
-// ------------------------------------------------------------------ load ----
-__global__ void load_kernel(int n, const float2* __restrict__ upos,
-                            const float2* __restrict__ uvel,
-                            const float* __restrict__ uradius,
-                            const uint8_t* __restrict__ utype, float2* __restrict__ pos0,
-                            float2* __restrict__ vel0, uint2* __restrict__ aux,
-                            uint32_t* __restrict__ count, int ncells, int* __restrict__ err) {
-    int stride = gridDim.x * blockDim.x;
-    int i0 = blockIdx.x * blockDim.x + threadIdx.x;
-    for (int c = i0; c < ncells; c += stride) count[c] = 0u;
-    bool bad = false;
-    for (int i = i0; i < n; i += stride) {
-        float2 p = upos[i], v = uvel[i];
-        bad |= !(isfinite(p.x) && isfinite(p.y) && isfinite(v.x) && isfinite(v.y));
-        pos0[i] = p;
-        vel0[i] = v;
-        aux[i] = aux_pack(uradius[i], utype[i], i);
-    }
-    if (bad) atomicOr(err, ERR_BIT_NONFINITE);
-}
-
-// ------------------------------------------------------------- bin count ----
-template <class SRC>
-__global__ void bin_count_kernel(int n, SRC src, const float2* __restrict__ pos,
-                                 uint32_t* __restrict__ key, uint32_t* __restrict__ slot,
-                                 uint32_t* __restrict__ count) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const SceneDev& sc = src.get(i);
-    float2 p = pos[i];
-    int cx = cell_axis(p.x, sc.origin_x, sc.inv_cell, sc.nx);
-    int cy = cell_axis(p.y, sc.origin_y, sc.inv_cell, sc.ny);
-    uint32_t c = (uint32_t)(sc.cell_off + cy * sc.nx + cx);
-    key[i] = c;
-    slot[i] = atomicAdd(count + c, 1u);
-}
 
 // ------------------------------------------------------------------ scan ----
 // Exclusive scan of the cell counts into cell starts, three phases: per-block
@@ -173,19 +136,238 @@ __global__ void scan_add_kernel(uint32_t* __restrict__ start, const uint32_t* __
     if (c == 0) start[ncells] = bsum[nb];
 }
 
-// --------------------------------------------------------------- scatter ----
-__global__ void scatter_kernel(int n, const uint32_t* __restrict__ key,
-                               const uint32_t* __restrict__ slot,
-                               const uint32_t* __restrict__ start,
-                               const float2* __restrict__ pos0, const float2* __restrict__ vel0,
-                               const uint2* __restrict__ aux_a, float2* __restrict__ pos1,
-                               float2* __restrict__ vel1, uint2* __restrict__ aux_b) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t s = start[key[i]] + slot[i];
-    pos1[s] = pos0[i];
-    vel1[s] = vel0[i];
-    aux_b[s] = aux_a[i];
+// ------------------------------------------------------------- binning ----
+// One cooperative launch per step sorts the agents by cell (counting sort):
+//   A  (first step of a call only) cell key and counter slot of every agent,
+//      from the caller's positions: one atomic increment of its cell count;
+//   B  every block sums the counts of its contiguous range of cells;
+//   C  every block adds up the sums of the blocks before it and scans its
+//      range into cell starts, clearing the counts for the next step;
+//   D  every agent's state moves to slot start[cell] + counter slot.
+// Later steps skip A: the solve kernel bins the new positions as it writes
+// them.  Grid barriers separate the phases.  The cooperative launch keeps
+// every block resident; a barrier that waits longer than about half a second
+// flags ERR_BIT_TIMEOUT and every block leaves the kernel.
+// The cell counts are zero on entry: the workspace is cleared once when a
+// scene is created, and phase C clears them again every step.  Should they
+// not sum to the agent count (a step cut short by a barrier that gave up, or
+// two calls on one workspace at once), the starts are clamped to the agent
+// count, agents whose slot falls outside are not moved, and ERR_BIT_STATE is
+// flagged: the step is wrong but stays inside its buffers.
+constexpr int kBinThreads = 256;
+constexpr int kBinUnroll = 4;        // agents in flight per thread in A and D
+constexpr int kBinGridMax = 4096;    // launch blocks at most (block-sum slots)
+constexpr unsigned kBarrierSpins = 1u << 22;
+
+struct BinArgs {
+    int n, ncells;
+    const float2* __restrict__ upos;   // caller arrays, caller order (first step)
+    const float2* __restrict__ uvel;
+    const float* __restrict__ urad;
+    const uint8_t* __restrict__ utype;
+    const float2* __restrict__ pos0;   // the previous solve's output (later steps)
+    const float2* __restrict__ vel0;
+    const uint2* __restrict__ aux0;
+    uint32_t* __restrict__ key;
+    uint32_t* __restrict__ slot;
+    uint32_t* __restrict__ count;
+    uint32_t* __restrict__ start;
+    uint32_t* __restrict__ bsum;
+    float2* __restrict__ pos1;         // sorted state
+    float2* __restrict__ vel1;
+    uint2* __restrict__ aux1;
+    int* __restrict__ err;             // [0] status bits; [2] arrivals, [3] generation
+    int test_skip_arrival;             // ORCA_DEBUG_BARRIER_TIMEOUT
+};
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier: bar[0] counts arrivals (the last block to arrive resets
+// it), bar[1] is the generation that the waiting blocks watch.  Returns false
+// in every thread of a block whose wait gave up.
+__device__ bool grid_barrier(unsigned* bar, int* err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        const unsigned gen = ld_acquire_gpu(bar + 1);
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicExch(bar + 1, gen + 1u);
+        } else {
+            unsigned it = 0;
+            while (ld_acquire_gpu(bar + 1) == gen) {
+                if (++it > kBarrierSpins) {
+                    atomicOr(err, ERR_BIT_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <class SRC, bool FIRST>
+__global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(SRC src, BinArgs a) {
+    __shared__ uint32_t ws[32];
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gs = gridDim.x * blockDim.x;
+    unsigned* bar = reinterpret_cast<unsigned*>(a.err + 2);
+    if (a.test_skip_arrival && blockIdx.x == 0) {
+        // failure-detection test: this block never arrives, the others' waits
+        // give up (a one-block grid flags the timeout itself)
+        if (threadIdx.x == 0) atomicOr(a.err, ERR_BIT_TIMEOUT);
+        return;
+    }
+
+    // ---- A: cell key and slot in the uniform grid (Sec. 1, grid-partitioned messaging) ----
+    if (FIRST) {
+        for (int i0 = gt; i0 < a.n; i0 += kBinUnroll * gs) {
+            float2 p[kBinUnroll];
+#pragma unroll
+            for (int u = 0; u < kBinUnroll; ++u) {
+                const int i = i0 + u * gs;
+                if (i < a.n) p[u] = a.upos[i];
+            }
+#pragma unroll
+            for (int u = 0; u < kBinUnroll; ++u) {
+                const int i = i0 + u * gs;
+                if (i < a.n) {
+                    const SceneDev& sc = src.get(i);
+                    const int cx = cell_axis(p[u].x, sc.origin_x, sc.inv_cell, sc.nx);
+                    const int cy = cell_axis(p[u].y, sc.origin_y, sc.inv_cell, sc.ny);
+                    const uint32_t c = (uint32_t)(sc.cell_off + cy * sc.nx + cx);
+                    a.key[i] = c;
+                    a.slot[i] = atomicAdd(a.count + c, 1u);
+                }
+            }
+        }
+        if (!grid_barrier(bar, a.err)) return;
+    }
+
+    // ---- B: block sums over contiguous cell ranges (multiples of 4) ----
+    const int chunk = (((a.ncells + (int)gridDim.x - 1) / (int)gridDim.x) + 3) & ~3;
+    const int c_lo = min((int)blockIdx.x * chunk, a.ncells);
+    const int c_hi = min(c_lo + chunk, a.ncells);
+    {
+        uint32_t sum = 0;
+        for (int c = c_lo + 4 * threadIdx.x; c < c_hi; c += 4 * blockDim.x) {
+            if (c + 4 <= c_hi) {
+                const uint4 x = __ldcg(reinterpret_cast<const uint4*>(a.count + c));
+                sum += x.x + x.y + x.z + x.w;
+            } else {
+                for (int q = c; q < c_hi; ++q) sum += __ldcg(a.count + q);
+            }
+        }
+        uint32_t total;
+        block_excl_scan(sum, ws, total);
+        if (threadIdx.x == 0) a.bsum[blockIdx.x] = total;
+    }
+    if (!grid_barrier(bar, a.err)) return;
+
+    // ---- C: cell starts (exclusive scan), counts cleared ----
+    {
+        uint32_t before = 0;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) before += __ldcg(a.bsum + b);
+        uint32_t carry;
+        block_excl_scan(before, ws, carry);
+        for (int c0 = c_lo; c0 < c_hi; c0 += 4 * blockDim.x) {
+            const int c = c0 + 4 * threadIdx.x;
+            const bool whole = c + 4 <= c_hi;
+            uint32_t v[4] = {0u, 0u, 0u, 0u};
+            if (whole) {
+                uint4* p4 = reinterpret_cast<uint4*>(a.count + c);
+                const uint4 x = __ldcg(p4);
+                v[0] = x.x;
+                v[1] = x.y;
+                v[2] = x.z;
+                v[3] = x.w;
+                *p4 = make_uint4(0u, 0u, 0u, 0u);
+            } else {
+                for (int q = 0; q < 4; ++q)
+                    if (c + q < c_hi) {
+                        v[q] = __ldcg(a.count + c + q);
+                        a.count[c + q] = 0u;
+                    }
+            }
+            uint32_t tile;
+            uint32_t o = carry + block_excl_scan(v[0] + v[1] + v[2] + v[3], ws, tile);
+            uint32_t st[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                st[q] = min(o, (uint32_t)a.n);
+                o += v[q];
+            }
+            if (whole) {
+                *reinterpret_cast<uint4*>(a.start + c) = make_uint4(st[0], st[1], st[2], st[3]);
+            } else {
+                for (int q = 0; q < 4; ++q)
+                    if (c + q < c_hi) a.start[c + q] = st[q];
+            }
+            carry += tile;
+        }
+        if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+            a.start[a.ncells] = min(carry, (uint32_t)a.n);
+            if (carry != (uint32_t)a.n) atomicOr(a.err, ERR_BIT_STATE);
+        }
+    }
+    if (!grid_barrier(bar, a.err)) return;
+
+    // ---- D: scatter the state to sorted slots ----
+    bool bad = false, lost = false;
+    for (int i0 = gt; i0 < a.n; i0 += kBinUnroll * gs) {
+        uint32_t d[kBinUnroll];
+#pragma unroll
+        for (int u = 0; u < kBinUnroll; ++u) {
+            const int i = i0 + u * gs;
+            if (i < a.n) d[u] = __ldcg(a.start + a.key[i]) + a.slot[i];
+        }
+        float2 p[kBinUnroll], v[kBinUnroll];
+        uint2 x[kBinUnroll];
+#pragma unroll
+        for (int u = 0; u < kBinUnroll; ++u) {
+            const int i = i0 + u * gs;
+            if (i < a.n) {
+                if (FIRST) {
+                    p[u] = a.upos[i];
+                    v[u] = a.uvel[i];
+                    x[u] = aux_pack(a.urad[i], a.utype[i], i);
+                } else {
+                    p[u] = a.pos0[i];
+                    v[u] = a.vel0[i];
+                    x[u] = a.aux0[i];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kBinUnroll; ++u) {
+            const int i = i0 + u * gs;
+            if (i < a.n) {
+                if (FIRST)
+                    bad |= !(isfinite(p[u].x) && isfinite(p[u].y) && isfinite(v[u].x) &&
+                             isfinite(v[u].y));
+                if (d[u] < (uint32_t)a.n) {
+                    a.pos1[d[u]] = p[u];
+                    a.vel1[d[u]] = v[u];
+                    a.aux1[d[u]] = x[u];
+                } else {
+                    lost = true;
+                }
+            }
+        }
+    }
+    if (bad) atomicOr(a.err, ERR_BIT_NONFINITE);
+    if (lost) atomicOr(a.err, ERR_BIT_STATE);
 }
 
 // ------------------------------------------------------- removal at goal ----
@@ -282,8 +464,12 @@ __global__ void __launch_bounds__(128)
 solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __restrict__ vel,
              const uint2* __restrict__ aux, const uint32_t* __restrict__ cstart,
              AgentIn ain, const float2* __restrict__ vpd, StepOut out, DebugOut dbg,
-             unsigned long long* __restrict__ counters) {
+             unsigned long long* __restrict__ counters, const int* __restrict__ err) {
     extern __shared__ float4 smem_lines[];
+    // after a binning kernel that gave up or found inconsistent counts the
+    // sorted state is not valid: leave everything as it is (the status call
+    // reports the error)
+    if (__ldcg(err) & (ERR_BIT_TIMEOUT | ERR_BIT_STATE)) return;
     const int stride = blockDim.x;
     float4* L = smem_lines + threadIdx.x;
     const int s_raw = blockIdx.x * blockDim.x + threadIdx.x;

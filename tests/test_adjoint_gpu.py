@@ -124,7 +124,7 @@ def test_checkpoint_interval_changes_nothing():
         assert np.array_equal(g["pos_T"], base["pos_T"])
         assert _rel(g["dvpd"], base["dvpd"]) <= 1e-5, k
         assert _rel(g["dwp"], base["dwp"]) <= 1e-5, k
-    assert base["launches"] == 2 + 6 * 13
+    assert base["launches"] == 3 * 13   # per step: replayed binning + solve, adjoint kernel
 
 
 def test_autograd_function_end_to_end():

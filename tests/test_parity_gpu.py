@@ -169,7 +169,7 @@ def test_nonfinite_input_reports_status():
 def test_launch_count():
     s = scenes.open_square(100, 10.0)
     ds = api.DeviceScene(s)
-    assert ds.launch_count(3) == 2 + 5 * 3
+    assert ds.launch_count(3) == 2 * 3   # binning + solve per step
     assert ds.launch_count(0) == 0
     ds.close()
 
