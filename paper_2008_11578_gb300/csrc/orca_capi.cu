@@ -35,7 +35,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // Workspace carve-up (device, caller owned).  The scene table and the scene
 // id of every slot exist only for batches (n_scenes > 0).
 struct Layout {
-    size_t err, count, start, bsum, key, slot, pos0, vel0, pos1, vel1;
+    size_t err, count, start, bsum, key, slot, hint, pos0, vel0, pos1, vel1;
     size_t aux[2];
     size_t scenes, sid;
     size_t total;
@@ -59,6 +59,7 @@ Layout make_layout(size_t n, size_t ncells, size_t n_scenes) {
     L.bsum = take((nb + 1) * 4);
     L.key = take(n * 4);
     L.slot = take((n + 1) * 4);   // + the total of the agent scan
+    L.hint = take(n * 4);
     L.pos0 = take(n * 8);
     L.vel0 = take(n * 8);
     L.pos1 = take(n * 8);
@@ -77,7 +78,7 @@ Layout make_layout(size_t n, size_t ncells, size_t n_scenes) {
 // Device pointers of one workspace.
 struct Buffers {
     int* err;
-    uint32_t *count, *start, *bsum, *key, *slot;
+    uint32_t *count, *start, *bsum, *key, *slot, *hint;
     float2 *pos0, *vel0, *pos1, *vel1;
     uint2* aux[2];
     SceneDev* scenes;
@@ -92,6 +93,7 @@ Buffers carve(char* w, const Layout& L, bool batch) {
     b.bsum = (uint32_t*)(w + L.bsum);
     b.key = (uint32_t*)(w + L.key);
     b.slot = (uint32_t*)(w + L.slot);
+    b.hint = (uint32_t*)(w + L.hint);
     b.pos0 = (float2*)(w + L.pos0);
     b.vel0 = (float2*)(w + L.vel0);
     b.pos1 = (float2*)(w + L.pos1);
@@ -281,7 +283,7 @@ void launch_bin(const Pipeline& P, SRC src, bool first, int cur, cudaStream_t st
     const orca_agents& A = P.agents;
     const BinArgs a{P.n, P.ncells, (const float2*)A.pos, (const float2*)A.vel, A.radius, A.type,
                     B.pos0, B.vel0, B.aux[cur], B.key, B.slot, B.count, B.start, B.bsum,
-                    B.pos1, B.vel1, B.aux[1 - cur], B.err,
+                    B.pos1, B.vel1, B.aux[1 - cur], B.err, B.hint,
                     (P.flags & ORCA_DEBUG_BARRIER_TIMEOUT) ? 1 : 0};
     const long long work = std::max((long long)P.n, (long long)P.ncells / 4);
     const int grid = (int)std::max(
@@ -326,8 +328,9 @@ void enqueue_steps(const Pipeline& P, SRC src, int n_steps, const float* vpref_d
         if (P.ev_begin) cudaEventRecord(P.ev_begin, st);
         const bool last = t == n_steps - 1;
         const StepOut out = last ? StepOut{(float2*)A.pos, (float2*)A.vel, true, nullptr, nullptr,
-                                           nullptr}
-                                 : StepOut{B.pos0, B.vel0, false, B.key, B.slot, B.count};
+                                           nullptr, B.hint, B.err + 1}
+                                 : StepOut{B.pos0, B.vel0, false, B.key, B.slot, B.count,
+                                           nullptr, nullptr};
         launch_solve(mode, sgrid, sb, smem, st, n, src, B.pos1, B.vel1, B.aux[cur], B.start,
                      ain, vpd, out, dbg_for(t), P.counters, B.err);
         if (P.ev_end) cudaEventRecord(P.ev_end, st);
@@ -773,6 +776,11 @@ int orca_scene_remove_arrived(orca_scene* s, int* n_kept, int32_t* kept_index, v
             (float2*)A.vel, (float2*)A.goal, (float*)A.radius, (float*)A.max_speed,
             (uint8_t*)A.type, (int32_t*)A.route, A.wp_idx, kept_index);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        return ORCA_ERR_CUDA;
+    // the recorded sorted order names the old indices: bin the next call in
+    // the caller's order
+    if (cudaMemsetAsync(B.err + 1, 0, 4, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
         return ORCA_ERR_CUDA;
     P.n = (int)kept;
     drop_graph(P);   // a graph recorded for the old count is stale

@@ -83,7 +83,9 @@ __device__ __forceinline__ int aux_type(uint2 a) { return (int)(a.y >> 31); }
 // next step's cell key and counter slot, which saves that step's bin_count
 // launch.  The last step of a call writes straight to the caller's arrays at
 // the original index instead (caller_order), so no separate kernel has to
-// copy the results back to the caller's order.
+// copy the results back to the caller's order.  It also records the original
+// index of every sorted slot (hint) and raises *hint_ok: the next call bins
+// its agents in that order, which is nearly the new cell order.
 struct StepOut {
     float2* pos;
     float2* vel;
@@ -91,6 +93,8 @@ struct StepOut {
     uint32_t* key;
     uint32_t* slot;
     uint32_t* count;
+    uint32_t* hint;
+    int* hint_ok;
 };
 
 // Optional per-agent outputs of the solve kernel, caller order, any of them

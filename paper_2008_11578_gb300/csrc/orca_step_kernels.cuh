@@ -176,7 +176,8 @@ struct BinArgs {
     float2* __restrict__ pos1;         // sorted state
     float2* __restrict__ vel1;
     uint2* __restrict__ aux1;
-    int* __restrict__ err;             // [0] status bits; [2] arrivals, [3] generation
+    int* __restrict__ err;             // [0] status bits, [1] hint valid; [2] arrivals, [3] generation
+    const uint32_t* __restrict__ hint; // first step: original index per previous sorted slot
     int test_skip_arrival;             // ORCA_DEBUG_BARRIER_TIMEOUT
 };
 
@@ -230,28 +231,60 @@ __global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(SRC src, BinArgs a)
         return;
     }
 
+    // Order of the first step's agents: the previous call's sorted order
+    // when its last step recorded it (the agents have barely moved, so
+    // neighbouring threads share cells), else the caller's order.  Any
+    // permutation gives the same result; indices are checked all the same.
+    const uint32_t* __restrict__ hint = nullptr;
+    if (FIRST && __ldcg(a.err + 1) != 0) hint = a.hint;
+    const int lane = threadIdx.x & 31;
+
     // ---- A: cell key and slot in the uniform grid (Sec. 1, grid-partitioned messaging) ----
     if (FIRST) {
-        for (int i0 = gt; i0 < a.n; i0 += kBinUnroll * gs) {
+        bool lost = false;
+        // i0 - lane is the same in a whole warp, so every lane runs the loop
+        // and the warp-wide vote below sees all of them
+        for (int i0 = gt; i0 - lane < a.n; i0 += kBinUnroll * gs) {
+            int oi[kBinUnroll];
             float2 p[kBinUnroll];
 #pragma unroll
             for (int u = 0; u < kBinUnroll; ++u) {
                 const int i = i0 + u * gs;
-                if (i < a.n) p[u] = a.upos[i];
+                oi[u] = -1;
+                if (i < a.n) {
+                    const uint32_t o = hint ? __ldg(hint + i) : (uint32_t)i;
+                    if (o < (uint32_t)a.n) {
+                        oi[u] = (int)o;
+                        p[u] = a.upos[o];
+                    } else {
+                        lost = true;
+                    }
+                }
             }
 #pragma unroll
             for (int u = 0; u < kBinUnroll; ++u) {
                 const int i = i0 + u * gs;
-                if (i < a.n) {
-                    const SceneDev& sc = src.get(i);
+                const bool valid = oi[u] >= 0;
+                const unsigned vm = __ballot_sync(0xffffffffu, valid);
+                if (valid) {
+                    const SceneDev& sc = src.get(oi[u]);
                     const int cx = cell_axis(p[u].x, sc.origin_x, sc.inv_cell, sc.nx);
                     const int cy = cell_axis(p[u].y, sc.origin_y, sc.inv_cell, sc.ny);
                     const uint32_t c = (uint32_t)(sc.cell_off + cy * sc.nx + cx);
+                    // one counter increment per distinct cell of the warp
+                    const unsigned grp = __match_any_sync(vm, c);
+                    const int leader = __ffs(grp) - 1;
+                    uint32_t base = 0u;
+                    if (lane == leader) base = atomicAdd(a.count + c, (uint32_t)__popc(grp));
+                    base = __shfl_sync(grp, base, leader);
                     a.key[i] = c;
-                    a.slot[i] = atomicAdd(a.count + c, 1u);
+                    a.slot[i] = base + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+                } else if (i < a.n) {
+                    a.key[i] = 0xffffffffu;   // out-of-range hint entry: not moved
                 }
             }
         }
+        if (lost) atomicOr(a.err, ERR_BIT_STATE);
         if (!grid_barrier(bar, a.err)) return;
     }
 
@@ -327,21 +360,29 @@ __global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(SRC src, BinArgs a)
     bool bad = false, lost = false;
     for (int i0 = gt; i0 < a.n; i0 += kBinUnroll * gs) {
         uint32_t d[kBinUnroll];
+        int oi[kBinUnroll];
 #pragma unroll
         for (int u = 0; u < kBinUnroll; ++u) {
             const int i = i0 + u * gs;
-            if (i < a.n) d[u] = __ldcg(a.start + a.key[i]) + a.slot[i];
+            d[u] = 0xffffffffu;
+            oi[u] = i;
+            if (i < a.n) {
+                const uint32_t c = a.key[i];
+                if (c < (uint32_t)a.ncells) d[u] = __ldcg(a.start + c) + a.slot[i];
+                if (FIRST) oi[u] = hint ? (int)__ldg(hint + i) : i;
+            }
         }
         float2 p[kBinUnroll], v[kBinUnroll];
         uint2 x[kBinUnroll];
 #pragma unroll
         for (int u = 0; u < kBinUnroll; ++u) {
             const int i = i0 + u * gs;
-            if (i < a.n) {
+            if (i < a.n && d[u] < (uint32_t)a.n) {
                 if (FIRST) {
-                    p[u] = a.upos[i];
-                    v[u] = a.uvel[i];
-                    x[u] = aux_pack(a.urad[i], a.utype[i], i);
+                    const int o = oi[u];   // in range: phase A checked it (key set)
+                    p[u] = a.upos[o];
+                    v[u] = a.uvel[o];
+                    x[u] = aux_pack(a.urad[o], a.utype[o], o);
                 } else {
                     p[u] = a.pos0[i];
                     v[u] = a.vel0[i];
@@ -353,10 +394,10 @@ __global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(SRC src, BinArgs a)
         for (int u = 0; u < kBinUnroll; ++u) {
             const int i = i0 + u * gs;
             if (i < a.n) {
-                if (FIRST)
-                    bad |= !(isfinite(p[u].x) && isfinite(p[u].y) && isfinite(v[u].x) &&
-                             isfinite(v[u].y));
                 if (d[u] < (uint32_t)a.n) {
+                    if (FIRST)
+                        bad |= !(isfinite(p[u].x) && isfinite(p[u].y) && isfinite(v[u].x) &&
+                                 isfinite(v[u].y));
                     a.pos1[d[u]] = p[u];
                     a.vel1[d[u]] = v[u];
                     a.aux1[d[u]] = x[u];
@@ -500,6 +541,35 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     const float R2 = sc.R2;
     const uint32_t* __restrict__ cs = cstart + sc.cell_off;
 
+    // candidate j at key distance d2: admitted when within R_n and its
+    // (d^2, original index) key is below the k-th; the entries behind it shift
+    auto consider = [&](int j, float d2) {
+        if (d2 < R2 && d2 <= thr_d && j != s) {
+            const int oj = aux_orig(__ldg(aux + j));
+            const unsigned long long key =
+                ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)oj;
+            if (key < thr_key) {
+                int at = min(cnt, k - 1);
+                while (at > 0) {
+                    const float4 e = L[(at - 1) * stride];
+                    const unsigned long long ek =
+                        ((unsigned long long)__float_as_uint(e.x) << 32) | __float_as_uint(e.z);
+                    if (ek < key) break;
+                    L[at * stride] = e;
+                    --at;
+                }
+                L[at * stride] = make_float4(d2, __int_as_float(j), __int_as_float(oj), 0.0f);
+                cnt = min(cnt + 1, k);
+                if (cnt == k) {
+                    const float4 e = L[(k - 1) * stride];
+                    thr_d = e.x;
+                    thr_key =
+                        ((unsigned long long)__float_as_uint(e.x) << 32) | __float_as_uint(e.z);
+                }
+            }
+        }
+    };
+
     if (k > 0) {
         const int nx = sc.nx, ny = sc.ny;
         const int mmax = max(max(cx, nx - 1 - cx), max(cy, ny - 1 - cy));
@@ -544,33 +614,14 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                 const int c0 = ry * nx + rx0, c1 = ry * nx + rx1;
                 const int jb = (int)__ldg(cs + c0), je = (int)__ldg(cs + c1 + 1);
                 n_cand += je - jb;
-                for (int j = jb; j < je; ++j) {
-                    const float2 q = pos[j];
-                    const float d2 = key_d2(p.x, p.y, q.x, q.y);
-                    if (d2 < R2 && d2 <= thr_d && j != s) {
-                        const int oj = aux_orig(__ldg(aux + j));
-                        const unsigned long long key =
-                            ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)oj;
-                        if (key < thr_key) {
-                            int at = min(cnt, k - 1);
-                            while (at > 0) {
-                                const float4 e = L[(at - 1) * stride];
-                                const unsigned long long ek =
-                                    ((unsigned long long)__float_as_uint(e.x) << 32) | __float_as_uint(e.z);
-                                if (ek < key) break;
-                                L[at * stride] = e;
-                                --at;
-                            }
-                            L[at * stride] =
-                                make_float4(d2, __int_as_float(j), __int_as_float(oj), 0.0f);
-                            cnt = min(cnt + 1, k);
-                            if (cnt == k) {
-                                const float4 e = L[(k - 1) * stride];
-                                thr_d = e.x;
-                                thr_key = ((unsigned long long)__float_as_uint(e.x) << 32) | __float_as_uint(e.z);
-                            }
-                        }
-                    }
+                // two candidates per iteration: both position loads in flight
+                for (int j = jb; j < je; j += 2) {
+                    const int j1 = min(j + 1, je - 1);
+                    const float2 q0 = pos[j], q1 = pos[j1];
+                    const float d0 = key_d2(p.x, p.y, q0.x, q0.y);
+                    const float d1 = j + 1 < je ? key_d2(p.x, p.y, q1.x, q1.y) : CUDART_INF_F;
+                    consider(j, d0);
+                    consider(j + 1, d1);
                 }
             }
             // every agent outside rings 0..m is farther than (m - delta) cells
@@ -699,6 +750,10 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     const int w = out.caller_order ? o : s;
     out.vel[w] = make_float2(vx, vy);
     out.pos[w] = pn;
+    if (out.hint != nullptr) {
+        out.hint[s] = (uint32_t)o;
+        if (s == 0) *out.hint_ok = 1;
+    }
     if (out.key != nullptr) {
         // bin the new position for the next step (as bin_count_kernel does)
         const int ncx = cell_axis(pn.x, sc.origin_x, sc.inv_cell, sc.nx);

@@ -112,6 +112,37 @@ def test_multi_step_call_equals_single_steps_and_is_deterministic():
     assert np.array_equal(a["pos"], c.pos) and np.array_equal(a["vel"], c.vel)
 
 
+def test_repeated_calls_bin_in_the_recorded_order_and_change_nothing():
+    # the last step of a call records its sorted order; the next call bins in
+    # that order, which must not change any result
+    import torch
+    s = scenes.open_square(3000, 80.0, seed=21)
+    a = gpu_step(s, n_steps=4, debug=False)
+    ds = api.DeviceScene(s, "cuda")
+    for _ in range(4):
+        ds.step(1)
+    torch.cuda.synchronize()
+    assert ds.sync_status() == 0
+    assert np.array_equal(ds.pos.cpu().numpy(), a["pos"])
+    assert np.array_equal(ds.vel.cpu().numpy(), a["vel"])
+    # the caller reorders its agents between calls: the recorded order is
+    # then an arbitrary permutation, still a valid one
+    perm = np.random.default_rng(3).permutation(s.n)
+    pt = torch.as_tensor(perm, device="cuda")
+    for t in (ds.pos, ds.vel, ds.goal, ds.radius, ds.max_speed, ds.type):
+        t.copy_(t[pt].clone())
+    c = s.copy()
+    c.pos, c.vel = a["pos"], a["vel"]
+    c = c.subset(perm)
+    ds.step(1)
+    torch.cuda.synchronize()
+    b = gpu_step(c, debug=False)
+    assert ds.sync_status() == 0
+    assert np.array_equal(ds.pos.cpu().numpy(), b["pos"])
+    assert np.array_equal(ds.vel.cpu().numpy(), b["vel"])
+    ds.close()
+
+
 # ------------------------------------------------------------ edge cases ----
 
 def test_empty_scene():
