@@ -282,7 +282,8 @@ void launch_bin(const Pipeline& P, SRC src, bool first, int cur, cudaStream_t st
     const Buffers& B = P.buf;
     const orca_agents& A = P.agents;
     const BinArgs a{P.n, P.ncells, (const float2*)A.pos, (const float2*)A.vel, A.radius, A.type,
-                    B.pos0, B.vel0, B.aux[cur], B.key, B.slot, B.count, B.start, B.bsum,
+                    B.pos0, B.vel0, B.aux[cur], B.pos0, B.vel0, B.aux[cur], B.key, B.slot,
+                    B.count, B.start, B.bsum,
                     B.pos1, B.vel1, B.aux[1 - cur], B.err, B.hint,
                     (P.flags & ORCA_DEBUG_BARRIER_TIMEOUT) ? 1 : 0};
     const long long work = std::max((long long)P.n, (long long)P.ncells / 4);

@@ -168,6 +168,9 @@ struct BinArgs {
     const float2* __restrict__ pos0;   // the previous solve's output (later steps)
     const float2* __restrict__ vel0;
     const uint2* __restrict__ aux0;
+    float2* __restrict__ stage_pos;    // first step: the caller's state in binning order
+    float2* __restrict__ stage_vel;
+    uint2* __restrict__ stage_aux;
     uint32_t* __restrict__ key;
     uint32_t* __restrict__ slot;
     uint32_t* __restrict__ count;
@@ -240,13 +243,17 @@ __global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(SRC src, BinArgs a)
     const int lane = threadIdx.x & 31;
 
     // ---- A: cell key and slot in the uniform grid (Sec. 1, grid-partitioned messaging) ----
+    // The caller's state is staged in this order (pos0, vel0, aux0), so the
+    // scatter below reads it sequentially, as on later steps.
     if (FIRST) {
-        bool lost = false;
+        bool lost = false, bad = false;
         // i0 - lane is the same in a whole warp, so every lane runs the loop
-        // and the warp-wide vote below sees all of them
+        // and the warp-wide votes below see all of them
         for (int i0 = gt; i0 - lane < a.n; i0 += kBinUnroll * gs) {
             int oi[kBinUnroll];
-            float2 p[kBinUnroll];
+            float2 p[kBinUnroll], v[kBinUnroll];
+            float rad[kBinUnroll];
+            int typ[kBinUnroll];
 #pragma unroll
             for (int u = 0; u < kBinUnroll; ++u) {
                 const int i = i0 + u * gs;
@@ -256,35 +263,56 @@ __global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(SRC src, BinArgs a)
                     if (o < (uint32_t)a.n) {
                         oi[u] = (int)o;
                         p[u] = a.upos[o];
+                        v[u] = a.uvel[o];
+                        rad[u] = a.urad[o];
+                        typ[u] = a.utype[o];
                     } else {
                         lost = true;
                     }
                 }
             }
+            uint32_t c[kBinUnroll], grp[kBinUnroll], base[kBinUnroll];
 #pragma unroll
             for (int u = 0; u < kBinUnroll; ++u) {
-                const int i = i0 + u * gs;
                 const bool valid = oi[u] >= 0;
                 const unsigned vm = __ballot_sync(0xffffffffu, valid);
+                c[u] = 0xffffffffu;
+                grp[u] = 0u;
                 if (valid) {
                     const SceneDev& sc = src.get(oi[u]);
                     const int cx = cell_axis(p[u].x, sc.origin_x, sc.inv_cell, sc.nx);
                     const int cy = cell_axis(p[u].y, sc.origin_y, sc.inv_cell, sc.ny);
-                    const uint32_t c = (uint32_t)(sc.cell_off + cy * sc.nx + cx);
-                    // one counter increment per distinct cell of the warp
-                    const unsigned grp = __match_any_sync(vm, c);
-                    const int leader = __ffs(grp) - 1;
-                    uint32_t base = 0u;
-                    if (lane == leader) base = atomicAdd(a.count + c, (uint32_t)__popc(grp));
-                    base = __shfl_sync(grp, base, leader);
-                    a.key[i] = c;
-                    a.slot[i] = base + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+                    c[u] = (uint32_t)(sc.cell_off + cy * sc.nx + cx);
+                    grp[u] = __match_any_sync(vm, c[u]);
+                }
+            }
+            // one counter increment per distinct cell of the warp; all of a
+            // thread's increments are issued before any result is used
+#pragma unroll
+            for (int u = 0; u < kBinUnroll; ++u) {
+                base[u] = 0u;
+                if (grp[u] != 0u && lane == __ffs(grp[u]) - 1)
+                    base[u] = atomicAdd(a.count + c[u], (uint32_t)__popc(grp[u]));
+            }
+#pragma unroll
+            for (int u = 0; u < kBinUnroll; ++u) {
+                const int i = i0 + u * gs;
+                if (grp[u] != 0u) {
+                    const uint32_t b0 = __shfl_sync(grp[u], base[u], __ffs(grp[u]) - 1);
+                    a.key[i] = c[u];
+                    a.slot[i] = b0 + (uint32_t)__popc(grp[u] & ((1u << lane) - 1u));
+                    bad |= !(isfinite(p[u].x) && isfinite(p[u].y) && isfinite(v[u].x) &&
+                             isfinite(v[u].y));
+                    a.stage_pos[i] = p[u];
+                    a.stage_vel[i] = v[u];
+                    a.stage_aux[i] = aux_pack(rad[u], typ[u], oi[u]);
                 } else if (i < a.n) {
-                    a.key[i] = 0xffffffffu;   // out-of-range hint entry: not moved
+                    a.key[i] = 0xffffffffu;   // out-of-range order entry: not moved
                 }
             }
         }
         if (lost) atomicOr(a.err, ERR_BIT_STATE);
+        if (bad) atomicOr(a.err, ERR_BIT_NONFINITE);
         if (!grid_barrier(bar, a.err)) return;
     }
 
@@ -357,19 +385,19 @@ __global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(SRC src, BinArgs a)
     if (!grid_barrier(bar, a.err)) return;
 
     // ---- D: scatter the state to sorted slots ----
-    bool bad = false, lost = false;
+    bool lost = false;
+    const float2* __restrict__ spos = FIRST ? a.stage_pos : a.pos0;
+    const float2* __restrict__ svel = FIRST ? a.stage_vel : a.vel0;
+    const uint2* __restrict__ saux = FIRST ? a.stage_aux : a.aux0;
     for (int i0 = gt; i0 < a.n; i0 += kBinUnroll * gs) {
         uint32_t d[kBinUnroll];
-        int oi[kBinUnroll];
 #pragma unroll
         for (int u = 0; u < kBinUnroll; ++u) {
             const int i = i0 + u * gs;
             d[u] = 0xffffffffu;
-            oi[u] = i;
             if (i < a.n) {
                 const uint32_t c = a.key[i];
                 if (c < (uint32_t)a.ncells) d[u] = __ldcg(a.start + c) + a.slot[i];
-                if (FIRST) oi[u] = hint ? (int)__ldg(hint + i) : i;
             }
         }
         float2 p[kBinUnroll], v[kBinUnroll];
@@ -378,16 +406,10 @@ __global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(SRC src, BinArgs a)
         for (int u = 0; u < kBinUnroll; ++u) {
             const int i = i0 + u * gs;
             if (i < a.n && d[u] < (uint32_t)a.n) {
-                if (FIRST) {
-                    const int o = oi[u];   // in range: phase A checked it (key set)
-                    p[u] = a.upos[o];
-                    v[u] = a.uvel[o];
-                    x[u] = aux_pack(a.urad[o], a.utype[o], o);
-                } else {
-                    p[u] = a.pos0[i];
-                    v[u] = a.vel0[i];
-                    x[u] = a.aux0[i];
-                }
+                // staged by this thread in phase A on a first step
+                p[u] = spos[i];
+                v[u] = svel[i];
+                x[u] = saux[i];
             }
         }
 #pragma unroll
@@ -395,9 +417,6 @@ __global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(SRC src, BinArgs a)
             const int i = i0 + u * gs;
             if (i < a.n) {
                 if (d[u] < (uint32_t)a.n) {
-                    if (FIRST)
-                        bad |= !(isfinite(p[u].x) && isfinite(p[u].y) && isfinite(v[u].x) &&
-                                 isfinite(v[u].y));
                     a.pos1[d[u]] = p[u];
                     a.vel1[d[u]] = v[u];
                     a.aux1[d[u]] = x[u];
@@ -407,7 +426,6 @@ __global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(SRC src, BinArgs a)
             }
         }
     }
-    if (bad) atomicOr(a.err, ERR_BIT_NONFINITE);
     if (lost) atomicOr(a.err, ERR_BIT_STATE);
 }
 

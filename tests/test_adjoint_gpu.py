@@ -264,8 +264,13 @@ def test_adjoint_against_oracle_finite_differences_on_the_workload():
     rng = np.random.default_rng(7)
     comps = []
     for key, arr, nnz, nany in (("d", c["dvpd"], 24, 6), ("w", gW, 10, 4)):
-        nz = np.argwhere(np.abs(arr) > 1e-7)
-        comps += [(key, tuple(x)) for x in nz[rng.permutation(len(nz))[:nnz]]]
+        # nonzero components, taken along a fixed random order of all indices:
+        # the float atomics of the chained VJPs add in a run-dependent order,
+        # and a component near the threshold that flips then changes one pick,
+        # not the whole sample
+        walk = [np.unravel_index(f, arr.shape) for f in rng.permutation(arr.size)]
+        comps += [(key, tuple(int(q) for q in ix)) for ix in
+                  [ix for ix in walk if abs(arr[ix]) > 1e-7][:nnz]]
         comps += [(key, tuple(int(rng.integers(0, m)) for m in arr.shape)) for _ in range(nany)]
     report, per_comp = {}, {}
     for h in (1e-3, 1e-5):
