@@ -420,7 +420,7 @@ def run_ours(args):
     scene, cfg = _scene(args.workload)
     n = scene.n
     tuned = None
-    cell, block = args.cell_size, 0
+    cell, block = args.cell_size, args.block_size
     if cell is None and not args.no_tune:
         # launch shape only: every candidate computes bit-identical states
         tuned = autotune.tune_scene(scene, dev, alphas=(1.0, 1.25, 1.5, 2.0), blocks=(64, 128),
@@ -577,6 +577,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="clusters_1m")
     ap.add_argument("--cell-size", type=float, default=None)
+    ap.add_argument("--block-size", type=int, default=0,
+                    help="solve block size with --cell-size (0: the library default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
