@@ -1,0 +1,100 @@
+"""Parity at the full sizes of the workloads, in the launch shapes the
+benchmark times, on outputs the oracle computes agent by agent.
+
+The benchmark advances the 1M-agent and 65k-agent scenes by one-step calls
+(every call bins its first step in the order the previous call recorded),
+and the 512-scene batch with the autotuner's cell factor and block size.
+Every test below does the same, then checks sampled agents of every step
+against the FP64 oracle from the identical FP32 state, and the cells of all
+agents bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_11578_gb300 import api, scenes
+from tests.parity_util import compare
+
+pytestmark = pytest.mark.gpu
+
+
+def _cells_oracle(scene, cell_size):
+    p = scene.params
+    nx, ny = p.grid_dims(cell_size)
+    return oracle.cells(scene.pos, p.origin, np.float32(1.0 / np.float32(cell_size)), nx, ny)
+
+
+def _calls(scene, cell_size, block_size, n_calls, n_sample, seed):
+    import torch
+    ds = api.DeviceScene(scene, "cuda", cell_size=cell_size, block_size=block_size, debug=True)
+    cur = scene.copy()
+    rng = np.random.default_rng(seed)
+    fallbacks = 0
+    for t in range(n_calls):
+        ds.step(1)
+        torch.cuda.synchronize()
+        assert ds.sync_status() == 0
+        g = dict(pos=ds.pos.cpu().numpy(), vel=ds.vel.cpu().numpy(),
+                 **{k: v.cpu().numpy() for k, v in ds.dbg.items()})
+        if ds.wp_idx is not None:
+            g["wp_idx"] = ds.wp_idx.cpu().numpy()
+        assert np.array_equal(g["cell"], _cells_oracle(cur, cell_size)), t
+        # every sample includes fallback agents (the least-penetration path)
+        inf = np.nonzero(g["flags"] & 1)[0]
+        sel = rng.choice(scene.n, n_sample, replace=False)
+        if len(inf):
+            sel = np.concatenate([sel, rng.choice(inf, min(len(inf), n_sample // 4), replace=False)])
+        st = compare(cur, g, sel=np.unique(sel))
+        fallbacks += st["infeasible_oracle"]
+        cur.pos, cur.vel = g["pos"], g["vel"]
+        if "wp_idx" in g:
+            cur.wp_idx = g["wp_idx"]
+    ds.close()
+    return fallbacks
+
+
+def test_clusters_1m_bench_shape_two_calls():
+    """990,000 pedestrians + 10,000 vehicles in 64 clusters over 2 x 2 km;
+    cell 1.5 m and solve block 64 (the autotuner's choice for this workload)."""
+    assert _calls(scenes.clusters(), 1.5, 64, 2, 3000, 1) > 1000
+
+
+def test_shared_space_65k_bench_shape_three_calls():
+    """64,000 pedestrians in two counter-flowing streams + 1,000 vehicles in
+    east-west lanes, 500 x 500 m."""
+    s = scenes.shared_space()
+    assert s.n == 65000
+    _calls(s, float(s.params.cell_size), 0, 3, 3000, 2)
+
+
+def test_batch_512_scenes_bench_shape():
+    """The 512-scene batch (1.79M agents) with the cell factor and block size
+    the autotuner picks for it (0.5 x each scene's cell, block 64): one step,
+    then the batch's graph of two more, checked on sampled scenes."""
+    import torch
+    sl = scenes.batched()
+    assert len(sl) == 512
+    b = api.DeviceBatch(sl, "cuda", cell_sizes=[0.5 * float(sc.params.cell_size) for sc in sl],
+                        block_size=64, debug=True)
+    rng = np.random.default_rng(5)
+    sizes = np.array([sc.n for sc in sl])
+    pick = np.unique(np.concatenate([rng.choice(len(sl), 24, replace=False),
+                                     [int(np.argmax(sizes)), int(np.argmin(sizes))]]))
+    cur = [sc.copy() for sc in sl]
+    for t in range(2):
+        b.step(1)
+        torch.cuda.synchronize()
+        assert b.sync_status() == 0
+        pos, vel = b.pos.cpu().numpy(), b.vel.cpu().numpy()
+        dbg = {k: v.cpu().numpy() for k, v in b.dbg.items()}
+        for s in pick:
+            r = b.scene_slice(int(s))
+            g = dict(pos=pos[r], vel=vel[r], cell=dbg["cell"][r], cnt=dbg["cnt"][r],
+                     flags=dbg["flags"][r],
+                     nbr=np.where(dbg["nbr"][r] >= 0, dbg["nbr"][r] - r.start, -1))
+            sel = np.sort(rng.choice(cur[s].n, min(cur[s].n, 200), replace=False))
+            compare(cur[s], g, sel=sel)
+        for s, sc in enumerate(cur):
+            r = b.scene_slice(s)
+            sc.pos, sc.vel = pos[r], vel[r]
+    b.close()

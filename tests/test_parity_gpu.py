@@ -64,8 +64,9 @@ def test_clusters_dense_sampled():
 
 
 def test_clusters_full_size_sampled():
-    """The 1M-agent workload at full size, launch configuration of the
-    benchmark; the oracle computes 3,000 sampled agents one by one."""
+    """The 1M-agent workload at full size in the library's default launch
+    shape (the benchmark's shape is in test_full_size_gpu.py); the oracle
+    computes 3,000 sampled agents one by one."""
     s = scenes.clusters()
     g = gpu_step(s)
     rng = np.random.default_rng(1)
