@@ -70,6 +70,11 @@ extern "C" {
    waits run out.  The step then reports ORCA_ERR_TIMEOUT through
    orca_scene_sync_status() and leaves the caller's arrays untouched. */
 #define ORCA_DEBUG_BARRIER_TIMEOUT 4u
+/* Solve the velocity LPs by active-set enumeration instead (every candidate
+   optimum of the 2D LP, then of the least-penetration LP, built and tested;
+   O(k^3) per agent, loops fixed by k).  For comparison; results agree with
+   the incremental LP to FP32 rounding.  Not with ORCA_FLAG_LP_WORK_UNITS. */
+#define ORCA_FLAG_LP_ENUMERATION 8u
 
 /*
  * Global parameters of one scene (Sec. 3 and 3.1).
@@ -85,8 +90,8 @@ extern "C" {
  *                   changes
  *   origin_x/y, grid_nx/ny   grid box; agents outside clamp to edge cells
  *   block_size      threads per block of the solve kernel (0 = 128)
- *   debug_flags     ORCA_DEBUG_NONE, or ORCA_FLAG_LP_WORK_UNITS and/or
- *                   ORCA_DEBUG_BARRIER_TIMEOUT
+ *   debug_flags     ORCA_DEBUG_NONE, or ORCA_FLAG_LP_WORK_UNITS or
+ *                   ORCA_FLAG_LP_ENUMERATION, and/or ORCA_DEBUG_BARRIER_TIMEOUT
  *   vehicle_turn_rate, vehicle_accel   kinematic limits of vehicles (type 1),
  *                   rad/s and m/s^2, 0 = off (default).  The paper names such
  *                   extra linear constraints as its extension for vehicles

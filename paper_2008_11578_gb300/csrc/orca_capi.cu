@@ -124,8 +124,11 @@ int check_params(const orca_params* p) {
         return ORCA_ERR_CAPACITY;
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 128 || p->block_size % 32))
         return ORCA_ERR_INVALID_ARG;
-    if (p->debug_flags & ~(unsigned)(ORCA_FLAG_LP_WORK_UNITS | ORCA_DEBUG_BARRIER_TIMEOUT))
+    if (p->debug_flags &
+        ~(unsigned)(ORCA_FLAG_LP_WORK_UNITS | ORCA_DEBUG_BARRIER_TIMEOUT | ORCA_FLAG_LP_ENUMERATION))
         return ORCA_ERR_INVALID_ARG;
+    if ((p->debug_flags & ORCA_FLAG_LP_WORK_UNITS) && (p->debug_flags & ORCA_FLAG_LP_ENUMERATION))
+        return ORCA_ERR_INVALID_ARG;   // one LP scheme at a time
     if (!std::isfinite(p->vehicle_turn_rate) || !std::isfinite(p->vehicle_accel) ||
         p->vehicle_turn_rate < 0.0f || p->vehicle_accel < 0.0f ||
         (double)p->vehicle_turn_rate * (double)p->dt >= 1.5707963267948966)
@@ -215,7 +218,10 @@ cudaError_t prepare_solve(size_t smem) {
         e = cudaFuncSetAttribute(solve_kernel<SRC, MODE_RECORD>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(solve_kernel<SRC, MODE_PLAIN, true>,
+        e = cudaFuncSetAttribute(solve_kernel<SRC, MODE_PLAIN, LP_WORK_UNITS>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(solve_kernel<SRC, MODE_PLAIN, LP_ENUMERATION>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return e;
 }
@@ -228,10 +234,11 @@ void launch_solve(int mode, int grid, int block, size_t smem, cudaStream_t st, i
 #define ORCA_SOLVE(M, W)                                                                    \
     solve_kernel<SRC, M, W><<<grid, block, smem, st>>>(n, src, pos, vel, aux, start, ain, vpd, \
                                                         out, dbg, counters, err)
-    if (mode == MODE_COUNT) ORCA_SOLVE(MODE_COUNT, false);
-    else if (mode == MODE_RECORD) ORCA_SOLVE(MODE_RECORD, false);
-    else if (mode == MODE_WORK_UNITS) ORCA_SOLVE(MODE_PLAIN, true);
-    else ORCA_SOLVE(MODE_PLAIN, false);
+    if (mode == MODE_COUNT) ORCA_SOLVE(MODE_COUNT, LP_INCREMENTAL);
+    else if (mode == MODE_RECORD) ORCA_SOLVE(MODE_RECORD, LP_INCREMENTAL);
+    else if (mode == MODE_WORK_UNITS) ORCA_SOLVE(MODE_PLAIN, LP_WORK_UNITS);
+    else if (mode == MODE_ENUMERATION) ORCA_SOLVE(MODE_PLAIN, LP_ENUMERATION);
+    else ORCA_SOLVE(MODE_PLAIN, LP_INCREMENTAL);
 #undef ORCA_SOLVE
 }
 
@@ -272,7 +279,8 @@ struct SameDebug {
 int step_mode(const Pipeline& P) {
     if (P.counters != nullptr) return MODE_COUNT;
     if (P.dbg.act != nullptr) return MODE_RECORD;
-    return (P.flags & ORCA_FLAG_LP_WORK_UNITS) ? MODE_WORK_UNITS : MODE_PLAIN;
+    if (P.flags & ORCA_FLAG_LP_WORK_UNITS) return MODE_WORK_UNITS;
+    return (P.flags & ORCA_FLAG_LP_ENUMERATION) ? MODE_ENUMERATION : MODE_PLAIN;
 }
 
 // The binning kernel of one step (cooperative launch, grid sized to what is

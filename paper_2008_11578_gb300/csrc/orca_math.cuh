@@ -580,4 +580,140 @@ __device__ __forceinline__ int solve_velocity_work_units(const float4* __restric
     return 1;
 }
 
+// ---------------------------------------------------------------------------
+// Active-set enumeration, for comparison: every point where the optimum can
+// sit is built and tested against all half-planes and the speed disc, in an
+// order that depends only on the number of lines.
+//   Admissible velocity: v_pref (its radial projection when faster than
+//   vmax); on every line the projection of v_pref clamped to the line's
+//   chord of the disc, and both chord ends; the crossing of every pair of
+//   lines.  The admissible candidate nearest v_pref is the optimum (Sec. 3,
+//   LP paragraphs), since the optimum of the projection onto a convex
+//   polygon cut by a disc is one of these points.
+//   Least penetration, when no candidate is admissible (Sec. 3,
+//   infeasible-set paragraph): t* = min over the disc of max_i det_i(v) is
+//   reached where three of {the planes det_i, the disc's rim} are active:
+//   the rim point of least penetration of one half-plane, the rim points
+//   where two half-planes penetrate equally, and the points where three do.
+//   The candidate with the smallest largest penetration wins, then the
+//   valley tie-break.
+// O(k^3) work per agent, against O(k^2) for the incremental scheme.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float max_penetration(const float4* __restrict__ L, int stride, int n,
+                                                 float x, float y) {
+    float t = -CUDART_INF_F;
+    for (int l = 0; l < n; ++l) t = fmaxf(t, penetration(L[l * stride], x, y));
+    return t;
+}
+
+__device__ __forceinline__ int solve_velocity_enumeration(const float4* __restrict__ L,
+                                                          int stride, int n, float vmax,
+                                                          float vpx, float vpy, float& vx,
+                                                          float& vy, float& tstar, int& work) {
+    const float tol = lp_tol(vmax);
+    // the disc, widened by the rounding of points built on its rim
+    const float r2 = vmax * vmax + 2.0f * tol * vmax;
+    float bd = CUDART_INF_F, bx = 0.0f, by = 0.0f;
+    auto offer = [&](float x, float y) {
+        if (x * x + y * y > r2) return;
+        if (max_penetration(L, stride, n, x, y) > tol) return;
+        const float dx = x - vpx, dy = y - vpy;
+        const float d = dx * dx + dy * dy;
+        if (d < bd) {
+            bd = d;
+            bx = x;
+            by = y;
+        }
+    };
+    {
+        const float vp2 = vpx * vpx + vpy * vpy;
+        if (vp2 > vmax * vmax) {
+            const float sc = vmax / sqrtf(vp2);
+            offer(vpx * sc, vpy * sc);
+        } else {
+            offer(vpx, vpy);
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        const float4 li = L[i * stride];
+        const float dot = li.x * li.z + li.y * li.w;
+        const float disc = dot * dot + vmax * vmax - (li.x * li.x + li.y * li.y);
+        if (disc < -tol * (1.0f + vmax)) continue;   // the line misses the disc
+        const float sq = sqrtf(fmaxf(disc, 0.0f));
+        const float tl = -dot - sq, tr = -dot + sq;
+        const float t0 = li.z * (vpx - li.x) + li.w * (vpy - li.y);
+        const float t = fminf(fmaxf(t0, tl), tr);
+        offer(li.x + t * li.z, li.y + t * li.w);
+        offer(li.x + tl * li.z, li.y + tl * li.w);
+        offer(li.x + tr * li.z, li.y + tr * li.w);
+        for (int j = 0; j < i; ++j) {
+            const float4 lj = L[j * stride];
+            const float den = li.z * lj.w - li.w * lj.z;                     // det(d_i, d_j)
+            if (den == 0.0f) continue;
+            const float num = lj.z * (li.y - lj.y) - lj.w * (li.x - lj.x);   // det(d_j, P_i - P_j)
+            const float tt = __fdividef(num, den);
+            offer(li.x + tt * li.z, li.y + tt * li.w);
+        }
+    }
+    work += n * (n + 1) / 2;
+    tstar = 0.0f;
+    if (bd < CUDART_INF_F) {
+        vx = bx;
+        vy = by;
+        return 0;
+    }
+    float bt = CUDART_INF_F;
+    auto offer3 = [&](float x, float y) {
+        if (x * x + y * y > r2) return;
+        const float t = max_penetration(L, stride, n, x, y);
+        if (t < bt) {
+            bt = t;
+            bx = x;
+            by = y;
+        }
+    };
+    for (int i = 0; i < n; ++i) {
+        const float4 li = L[i * stride];
+        const float ci = li.z * li.y - li.w * li.x;   // c = det(d, P), pen(v) = c - n . v
+        offer3(-li.w * vmax, li.z * vmax);            // vmax n_i, n = (-d_y, d_x)
+        for (int j = 0; j < i; ++j) {
+            const float4 lj = L[j * stride];
+            float4 bij;
+            if (!bisector(li, lj, bij)) continue;
+            const float dot = bij.x * bij.z + bij.y * bij.w;
+            const float disc = dot * dot + vmax * vmax - (bij.x * bij.x + bij.y * bij.y);
+            if (disc >= 0.0f) {
+                const float sq = sqrtf(disc);
+                offer3(bij.x + (-dot - sq) * bij.z, bij.y + (-dot - sq) * bij.w);
+                offer3(bij.x + (-dot + sq) * bij.z, bij.y + (-dot + sq) * bij.w);
+            }
+            // pen_i = pen_j = pen_m: (n_j - n_i) . v = c_j - c_i and
+            // (n_m - n_i) . v = c_m - c_i, by Cramer's rule
+            const float a1x = li.w - lj.w, a1y = lj.z - li.z;
+            const float b1 = (lj.z * lj.y - lj.w * lj.x) - ci;
+            const float n1 = sqrtf(a1x * a1x + a1y * a1y);
+            for (int m = 0; m < j; ++m) {
+                const float4 lm = L[m * stride];
+                const float a2x = li.w - lm.w, a2y = lm.z - li.z;
+                const float b2 = (lm.z * lm.y - lm.w * lm.x) - ci;
+                const float det = a1x * a2y - a1y * a2x;
+                // sine between the two normals: skip (near-)parallel pairs
+                if (fabsf(det) < 1e-6f * n1 * sqrtf(a2x * a2x + a2y * a2y)) continue;
+                offer3((b1 * a2y - b2 * a1y) / det, (a1x * b2 - a2x * b1) / det);
+            }
+        }
+    }
+    work += n * (n - 1) * (n + 1) / 6;
+    tstar = bt;
+    vx = bx;
+    vy = by;
+    float ox, oy;
+    uint32_t act = 0u;
+    if (valley_tie_break(L, stride, n, bt, vmax, vpx, vpy, bx, by, ox, oy, work, act)) {
+        vx = ox;
+        vy = oy;
+    }
+    return 1;
+}
+
 }  // namespace orca

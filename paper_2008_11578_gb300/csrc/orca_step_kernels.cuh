@@ -515,10 +515,11 @@ __global__ void compact_scatter_kernel(int kept, const float2* __restrict__ t_po
 // of thread t at [i * blockDim.x + t] (conflict-free float4).
 // MODE_COUNT adds work tallies (algorithmic FLOP accounting) and
 // MODE_RECORD the LP's active set; both are dead code in MODE_PLAIN.
-// WORK_UNITS solves the 2D LPs with the paper's block-cooperative work units
-// (comparison only); every thread of a block then takes part to the end of
-// the LP, lanes past the last agent shadowing it and writing nothing.
-template <class SRC, int MODE, bool WORK_UNITS = false>
+// LP selects the velocity-LP scheme: the incremental per-thread LP, or for
+// comparison only the paper's block-cooperative work units (every thread of a
+// block then takes part to the end of the LP, lanes past the last agent
+// shadowing it and writing nothing) or active-set enumeration.
+template <class SRC, int MODE, int LP = LP_INCREMENTAL>
 __global__ void __launch_bounds__(128)
 solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __restrict__ vel,
              const uint2* __restrict__ aux, const uint32_t* __restrict__ cstart,
@@ -532,6 +533,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     const int stride = blockDim.x;
     float4* L = smem_lines + threadIdx.x;
     const int s_raw = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr bool WORK_UNITS = LP == LP_WORK_UNITS;
     if (!WORK_UNITS && s_raw >= n) return;
     const bool active = s_raw < n;
     const int s = active ? s_raw : n - 1;
@@ -755,9 +757,10 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     float vx, vy, tstar;
     uint32_t act = 0u;
     const int infeasible =
-        WORK_UNITS
-            ? solve_velocity_work_units(smem_lines, active ? nlines : 0, vmax, vpx, vpy, vx, vy,
-                                        tstar, work)
+        WORK_UNITS ? solve_velocity_work_units(smem_lines, active ? nlines : 0, vmax, vpx, vpy,
+                                               vx, vy, tstar, work)
+        : LP == LP_ENUMERATION
+            ? solve_velocity_enumeration(L, stride, nlines, vmax, vpx, vpy, vx, vy, tstar, work)
             : solve_velocity(L, stride, nlines, vmax, vpx, vpy, vx, vy, tstar, work, act);
     if (!active) return;
     const uint8_t flags = (uint8_t)(infeasible | (any_overlap ? 4 : 0));
