@@ -378,15 +378,16 @@ def measure_adjoint(dev, n_steps=40, ckpt_every=8, reps=5):
 
 def measure_lp_schemes(scene, dev, cell, block, pos, vel, steps=5):
     """The per-thread incremental LP against the paper's work-unit batch LP
-    (Sec. 3) and against active-set enumeration, same workload, launch shape
-    and start state (``pos``/``vel``): median solve-kernel time over
-    ``steps`` single steps (the three agree to FP32 rounding)."""
+    (Sec. 3), the warp-cooperative LP and active-set enumeration, same
+    workload, launch shape and start state (``pos``/``vel``): median
+    solve-kernel time over ``steps`` single steps (all agree to FP32
+    rounding)."""
     import torch
 
     from paper_2008_11578_gb300 import api
     out = {}
     for name, flags in (("per_thread", 0), ("work_units", api.LP_WORK_UNITS),
-                        ("enumeration", api.LP_ENUMERATION)):
+                        ("warp", api.LP_WARP), ("enumeration", api.LP_ENUMERATION)):
         ds = api.DeviceScene(scene, dev, cell_size=cell, block_size=block, flags=flags)
         p0, v0 = pos.clone(), vel.clone()
         b, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -402,6 +403,7 @@ def measure_lp_schemes(scene, dev, cell, block, pos, vel, steps=5):
         out[name + "_solve_ms"] = statistics.median(ts)
         ds.close()
     out["work_units_over_per_thread"] = out["work_units_solve_ms"] / out["per_thread_solve_ms"]
+    out["warp_over_per_thread"] = out["warp_solve_ms"] / out["per_thread_solve_ms"]
     out["enumeration_over_per_thread"] = out["enumeration_solve_ms"] / out["per_thread_solve_ms"]
     return out
 

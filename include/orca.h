@@ -73,8 +73,14 @@ extern "C" {
 /* Solve the velocity LPs by active-set enumeration instead (every candidate
    optimum of the 2D LP, then of the least-penetration LP, built and tested;
    O(k^3) per agent, loops fixed by k).  For comparison; results agree with
-   the incremental LP to FP32 rounding.  Not with ORCA_FLAG_LP_WORK_UNITS. */
+   the incremental LP to FP32 rounding.  One LP-scheme flag at a time. */
 #define ORCA_FLAG_LP_ENUMERATION 8u
+/* Solve the velocity LPs warp-cooperatively instead (a warp takes its 32
+   agents' LPs one after another, its lanes splitting the constraints of each
+   1D sub-problem, merged by warp min/max reductions).  For comparison;
+   results agree with the incremental LP to FP32 rounding.  One LP-scheme
+   flag at a time. */
+#define ORCA_FLAG_LP_WARP 16u
 
 /*
  * Global parameters of one scene (Sec. 3 and 3.1).
@@ -90,8 +96,9 @@ extern "C" {
  *                   changes
  *   origin_x/y, grid_nx/ny   grid box; agents outside clamp to edge cells
  *   block_size      threads per block of the solve kernel (0 = 128)
- *   debug_flags     ORCA_DEBUG_NONE, or ORCA_FLAG_LP_WORK_UNITS or
- *                   ORCA_FLAG_LP_ENUMERATION, and/or ORCA_DEBUG_BARRIER_TIMEOUT
+ *   debug_flags     ORCA_DEBUG_NONE, or one of ORCA_FLAG_LP_WORK_UNITS,
+ *                   ORCA_FLAG_LP_ENUMERATION, ORCA_FLAG_LP_WARP, and/or
+ *                   ORCA_DEBUG_BARRIER_TIMEOUT
  *   vehicle_turn_rate, vehicle_accel   kinematic limits of vehicles (type 1),
  *                   rad/s and m/s^2, 0 = off (default).  The paper names such
  *                   extra linear constraints as its extension for vehicles

@@ -124,11 +124,11 @@ int check_params(const orca_params* p) {
         return ORCA_ERR_CAPACITY;
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 128 || p->block_size % 32))
         return ORCA_ERR_INVALID_ARG;
-    if (p->debug_flags &
-        ~(unsigned)(ORCA_FLAG_LP_WORK_UNITS | ORCA_DEBUG_BARRIER_TIMEOUT | ORCA_FLAG_LP_ENUMERATION))
-        return ORCA_ERR_INVALID_ARG;
-    if ((p->debug_flags & ORCA_FLAG_LP_WORK_UNITS) && (p->debug_flags & ORCA_FLAG_LP_ENUMERATION))
-        return ORCA_ERR_INVALID_ARG;   // one LP scheme at a time
+    const unsigned schemes =
+        ORCA_FLAG_LP_WORK_UNITS | ORCA_FLAG_LP_ENUMERATION | ORCA_FLAG_LP_WARP;
+    if (p->debug_flags & ~(schemes | ORCA_DEBUG_BARRIER_TIMEOUT)) return ORCA_ERR_INVALID_ARG;
+    const unsigned scheme = p->debug_flags & schemes;
+    if (scheme & (scheme - 1u)) return ORCA_ERR_INVALID_ARG;   // one LP scheme at a time
     if (!std::isfinite(p->vehicle_turn_rate) || !std::isfinite(p->vehicle_accel) ||
         p->vehicle_turn_rate < 0.0f || p->vehicle_accel < 0.0f ||
         (double)p->vehicle_turn_rate * (double)p->dt >= 1.5707963267948966)
@@ -223,6 +223,9 @@ cudaError_t prepare_solve(size_t smem) {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(solve_kernel<SRC, MODE_PLAIN, LP_ENUMERATION>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(solve_kernel<SRC, MODE_PLAIN, LP_WARP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return e;
 }
 
@@ -238,6 +241,7 @@ void launch_solve(int mode, int grid, int block, size_t smem, cudaStream_t st, i
     else if (mode == MODE_RECORD) ORCA_SOLVE(MODE_RECORD, LP_INCREMENTAL);
     else if (mode == MODE_WORK_UNITS) ORCA_SOLVE(MODE_PLAIN, LP_WORK_UNITS);
     else if (mode == MODE_ENUMERATION) ORCA_SOLVE(MODE_PLAIN, LP_ENUMERATION);
+    else if (mode == MODE_WARP_LP) ORCA_SOLVE(MODE_PLAIN, LP_WARP);
     else ORCA_SOLVE(MODE_PLAIN, LP_INCREMENTAL);
 #undef ORCA_SOLVE
 }
@@ -280,6 +284,7 @@ int step_mode(const Pipeline& P) {
     if (P.counters != nullptr) return MODE_COUNT;
     if (P.dbg.act != nullptr) return MODE_RECORD;
     if (P.flags & ORCA_FLAG_LP_WORK_UNITS) return MODE_WORK_UNITS;
+    if (P.flags & ORCA_FLAG_LP_WARP) return MODE_WARP_LP;
     return (P.flags & ORCA_FLAG_LP_ENUMERATION) ? MODE_ENUMERATION : MODE_PLAIN;
 }
 

@@ -120,9 +120,9 @@ struct DebugOut {
 constexpr int MODE_PLAIN = 0, MODE_COUNT = 1, MODE_RECORD = 2;
 // host-side choice of the plain variant with the paper's work-unit LP, or
 // with active-set enumeration
-constexpr int MODE_WORK_UNITS = 3, MODE_ENUMERATION = 4;
+constexpr int MODE_WORK_UNITS = 3, MODE_ENUMERATION = 4, MODE_WARP_LP = 5;
 // the solve kernel's velocity-LP scheme
-constexpr int LP_INCREMENTAL = 0, LP_WORK_UNITS = 1, LP_ENUMERATION = 2;
+constexpr int LP_INCREMENTAL = 0, LP_WORK_UNITS = 1, LP_ENUMERATION = 2, LP_WARP = 3;
 
 // Work tallies of the counting variant of the solve kernel:
 // [0] candidate key tests, [1] ORCA lines built, [2] LP pair evaluations

@@ -716,4 +716,181 @@ __device__ __forceinline__ int solve_velocity_enumeration(const float4* __restri
     return 1;
 }
 
+// ---------------------------------------------------------------------------
+// Warp-cooperative LP, for comparison: a warp solves the LPs of its 32
+// agents one after another, and within each 1D sub-problem (a line against
+// the earlier lines, or a bisector against the earlier planes) lane j takes
+// constraint j.  The interval ends are merged by warp reductions on
+// order-preserving integer images of the bounds (exact min and max), so the
+// result equals the per-thread LP's up to how the compiler contracts the
+// bounds' multiply-adds.  Every lane of the warp must call it (lanes without
+// an agent with n = 0).  lines_base is the block's line array (agent a,
+// line j at [j * B + a]); warp0 is the block index of the warp's lane 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_fmax(float x) {
+    return o2f(__reduce_max_sync(0xffffffffu, f2o(x)));
+}
+__device__ __forceinline__ float warp_fmin(float x) {
+    return o2f(__reduce_min_sync(0xffffffffu, f2o(x)));
+}
+
+// 1D problem on line li against lines 0..i-1 of La: the interval [tl, tr]
+// of li inside the disc and the earlier half-planes; false when empty.
+__device__ __forceinline__ bool warp_lp1_interval(const float4* __restrict__ La, int B, int i,
+                                                  float4 li, float vmax, float tol, float& tl,
+                                                  float& tr) {
+    const float dot = li.x * li.z + li.y * li.w;
+    const float disc = dot * dot + vmax * vmax - (li.x * li.x + li.y * li.y);
+    if (disc < -tol * (1.0f + vmax)) return false;
+    const float sq = sqrtf(fmaxf(disc, 0.0f));
+    float lo = -dot - sq, hi = -dot + sq;
+    bool empty = false;
+    const int lane = threadIdx.x & 31;
+    for (int j0 = 0; j0 < i; j0 += 32) {
+        const int j = j0 + lane;
+        float blo = -CUDART_INF_F, bhi = CUDART_INF_F;
+        if (j < i) {
+            const float4 lj = La[j * B];
+            const float den = li.z * lj.w - li.w * lj.z;                     // det(d_i, d_j)
+            const float num = lj.z * (li.y - lj.y) - lj.w * (li.x - lj.x);   // det(d_j, P_i - P_j)
+            if (den == 0.0f) {
+                empty |= num < -tol;
+            } else {
+                const float t = __fdividef(num, den);
+                if (den > 0.0f) bhi = t;
+                else blo = t;
+            }
+        }
+        lo = fmaxf(lo, warp_fmax(blo));
+        hi = fminf(hi, warp_fmin(bhi));
+    }
+    if (__any_sync(0xffffffffu, empty)) return false;
+    tl = lo;
+    tr = hi;
+    return !(lo > hi + tol);
+}
+
+__device__ __forceinline__ int solve_velocity_warp(const float4* __restrict__ lines_base,
+                                                   int warp0, int n_own, float vmax_own,
+                                                   float vpx_own, float vpy_own, float& vx,
+                                                   float& vy, float& tstar, int& work) {
+    const int lane = threadIdx.x & 31, B = blockDim.x;
+    int infeasible = 0;
+    vx = vy = tstar = 0.0f;
+    for (int a = 0; a < 32; ++a) {
+        const int n = __shfl_sync(0xffffffffu, n_own, a);
+        const float vmax = __shfl_sync(0xffffffffu, vmax_own, a);
+        const float vpx = __shfl_sync(0xffffffffu, vpx_own, a);
+        const float vpy = __shfl_sync(0xffffffffu, vpy_own, a);
+        const float4* La = lines_base + warp0 + a;
+        const float tol = lp_tol(vmax);
+        // ---- projection of v_pref (incremental over the lines) ----
+        float ox, oy;
+        const float vp2 = vpx * vpx + vpy * vpy;
+        if (vp2 > vmax * vmax) {
+            const float sc = vmax / sqrtf(vp2);
+            ox = vpx * sc;
+            oy = vpy * sc;
+        } else {
+            ox = vpx;
+            oy = vpy;
+        }
+        bool feasible = true;
+        for (int i = 0; i < n && feasible; ++i) {
+            const float4 li = La[i * B];
+            if (penetration(li, ox, oy) <= 0.0f) continue;
+            float tl, tr;
+            work += (i + 31) / 32;
+            if (!warp_lp1_interval(La, B, i, li, vmax, tol, tl, tr)) {
+                feasible = false;
+                break;
+            }
+            const float t0 = li.z * (vpx - li.x) + li.w * (vpy - li.y);
+            const float t = fminf(fmaxf(t0, tl), tr);
+            ox = li.x + t * li.z;
+            oy = li.y + t * li.w;
+        }
+        float ts = 0.0f;
+        if (!feasible) {
+            // ---- least penetration (incremental LP in (v, t)) ----
+            const float4 l0 = La[0];
+            float cx0 = -l0.w * vmax, cy0 = l0.z * vmax;
+            float t = penetration(l0, cx0, cy0);
+            for (int i = 1; i < n; ++i) {
+                const float4 li = La[i * B];
+                if (penetration(li, cx0, cy0) <= t) continue;
+                const float nix = -li.w, niy = li.z;
+                float cx = vmax * nix, cy = vmax * niy;
+                const float ci = li.z * li.y - li.w * li.x;
+                for (int j = 0; j < i; ++j) {
+                    const float4 lj = La[j * B];
+                    {
+                        const float ax = li.w - lj.w, ay = lj.z - li.z;
+                        const float beta = (lj.z * lj.y - lj.w * lj.x) - ci;
+                        if (beta - (ax * cx + ay * cy) <= 0.0f) continue;
+                    }
+                    float4 bj;
+                    if (!bisector(li, lj, bj)) continue;
+                    const float dot = bj.x * bj.z + bj.y * bj.w;
+                    const float disc = dot * dot + vmax * vmax - (bj.x * bj.x + bj.y * bj.y);
+                    if (disc < -tol * (1.0f + vmax)) continue;
+                    const float sq = sqrtf(fmaxf(disc, 0.0f));
+                    float lo = -dot - sq, hi = -dot + sq;
+                    bool bad = false;
+                    work += (j + 31) / 32;
+                    for (int k0 = 0; k0 < j; k0 += 32) {
+                        const int jj = k0 + lane;
+                        float blo = -CUDART_INF_F, bhi = CUDART_INF_F;
+                        if (jj < j) {
+                            const float4 lk = La[jj * B];
+                            const float ax = li.w - lk.w, ay = lk.z - li.z;   // n_jj - n_i
+                            if (ax * ax + ay * ay > 1e-12f) {
+                                const float beta = (lk.z * lk.y - lk.w * lk.x) - ci;
+                                const float den = ax * bj.z + ay * bj.w;
+                                const float num = beta - (ax * bj.x + ay * bj.y);
+                                if (den == 0.0f) {
+                                    bad |= num > tol;
+                                } else {
+                                    const float tt = __fdividef(num, den);
+                                    if (den < 0.0f) bhi = tt;
+                                    else blo = tt;
+                                }
+                            }
+                        }
+                        lo = fmaxf(lo, warp_fmax(blo));
+                        hi = fminf(hi, warp_fmin(bhi));
+                    }
+                    if (__any_sync(0xffffffffu, bad) || lo > hi + tol) continue;
+                    const bool right = nix * bj.z + niy * bj.w > 0.0f;
+                    const float tt = right ? hi : lo;
+                    cx = bj.x + tt * bj.z;
+                    cy = bj.y + tt * bj.w;
+                }
+                cx0 = cx;
+                cy0 = cy;
+                t = penetration(li, cx0, cy0);
+            }
+            float tm = -CUDART_INF_F;
+            for (int i = 0; i < n; ++i) tm = fmaxf(tm, penetration(La[i * B], cx0, cy0));
+            ts = tm;
+            ox = cx0;
+            oy = cy0;
+            float vx2, vy2;
+            uint32_t act = 0u;
+            int w2 = 0;
+            if (valley_tie_break(La, B, n, tm, vmax, vpx, vpy, cx0, cy0, vx2, vy2, w2, act)) {
+                ox = vx2;
+                oy = vy2;
+            }
+        }
+        if (lane == a) {
+            vx = ox;
+            vy = oy;
+            tstar = ts;
+            infeasible = feasible ? 0 : 1;
+        }
+    }
+    return infeasible;
+}
+
 }  // namespace orca

@@ -516,9 +516,10 @@ __global__ void compact_scatter_kernel(int kept, const float2* __restrict__ t_po
 // MODE_COUNT adds work tallies (algorithmic FLOP accounting) and
 // MODE_RECORD the LP's active set; both are dead code in MODE_PLAIN.
 // LP selects the velocity-LP scheme: the incremental per-thread LP, or for
-// comparison only the paper's block-cooperative work units (every thread of a
-// block then takes part to the end of the LP, lanes past the last agent
-// shadowing it and writing nothing) or active-set enumeration.
+// comparison only the paper's block-cooperative work units, the
+// warp-cooperative LP (with both, every thread of the block takes part to the
+// end of the LP, lanes past the last agent shadowing it and writing nothing)
+// or active-set enumeration.
 template <class SRC, int MODE, int LP = LP_INCREMENTAL>
 __global__ void __launch_bounds__(128)
 solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __restrict__ vel,
@@ -534,7 +535,8 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     float4* L = smem_lines + threadIdx.x;
     const int s_raw = blockIdx.x * blockDim.x + threadIdx.x;
     constexpr bool WORK_UNITS = LP == LP_WORK_UNITS;
-    if (!WORK_UNITS && s_raw >= n) return;
+    constexpr bool ALL_LANES = WORK_UNITS || LP == LP_WARP;
+    if (!ALL_LANES && s_raw >= n) return;
     const bool active = s_raw < n;
     const int s = active ? s_raw : n - 1;
     const SceneDev& sc = src.get(s);
@@ -759,6 +761,9 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     const int infeasible =
         WORK_UNITS ? solve_velocity_work_units(smem_lines, active ? nlines : 0, vmax, vpx, vpy,
                                                vx, vy, tstar, work)
+        : LP == LP_WARP
+            ? solve_velocity_warp(smem_lines, (int)(threadIdx.x & ~31u), active ? nlines : 0, vmax,
+                                  vpx, vpy, vx, vy, tstar, work)
         : LP == LP_ENUMERATION
             ? solve_velocity_enumeration(L, stride, nlines, vmax, vpx, vpy, vx, vy, tstar, work)
             : solve_velocity(L, stride, nlines, vmax, vpx, vpy, vx, vy, tstar, work, act);

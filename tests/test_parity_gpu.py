@@ -252,28 +252,31 @@ def test_vehicle_at_full_speed_on_its_own_half_plane_apex():
     assert (g["flags"][veh] & 1).sum() == 0
 
 
+@pytest.mark.parametrize("scheme", ["work_units", "warp"])
 @pytest.mark.parametrize("name", ["open_square", "clusters", "shared_space"])
-def test_work_unit_lp_matches_per_thread_lp(name):
-    """The paper's block-cooperative work-unit LP (the comparison variant)
-    computes the same intervals as the per-thread LP (up to the rounding of
-    differently contracted multiply-adds), so one step agrees to 1e-5; and it
-    agrees with the oracle like the per-thread LP does."""
+def test_cooperative_lp_matches_per_thread_lp(name, scheme):
+    """The paper's block-cooperative work-unit LP and the warp-cooperative LP
+    (the comparison variants) compute the same intervals as the per-thread LP
+    (min and max are exact; only differently contracted multiply-adds round
+    differently), so one step agrees to 1e-5; and they agree with the oracle
+    like the per-thread LP does."""
     import torch
     s = {"open_square": lambda: scenes.open_square(3000, 80.0, seed=61),
          "clusters": lambda: scenes.clusters(n=62500, side=500.0, n_clusters_axis=2),
          "shared_space": lambda: scenes.shared_space(n_ped=6400, n_veh=100, side=160.0)}[name]()
+    flag = {"work_units": api.LP_WORK_UNITS, "warp": api.LP_WARP}[scheme]
     out = {}
-    for flags in (0, api.LP_WORK_UNITS):
+    for flags in (0, flag):
         ds = api.DeviceScene(s, "cuda", debug=True, flags=flags)
         ds.step(1)
         torch.cuda.synchronize()
         assert ds.sync_status() == 0
         out[flags] = (ds.pos.cpu().numpy(), ds.vel.cpu().numpy())
         ds.close()
-    a, b = out[0], out[api.LP_WORK_UNITS]
+    a, b = out[0], out[flag]
     assert np.abs(a[1].astype(np.float64) - b[1]).max() <= 1e-5
     assert np.abs(a[0].astype(np.float64) - b[0]).max() <= 1e-5
-    g = gpu_step(s, flags=api.LP_WORK_UNITS)
+    g = gpu_step(s, flags=flag)
     compare(s, g, sel=np.arange(0, s.n, max(1, s.n // 3000)))
 
 
