@@ -50,6 +50,7 @@ extern "C" {
 #define ORCA_ERR_TIMEOUT 3       /* a bounded device wait gave up */
 #define ORCA_ERR_NONFINITE 4     /* a position or velocity was NaN/Inf */
 #define ORCA_ERR_CAPACITY 5      /* k above ORCA_MAX_NEIGHBORS, grid too large */
+#define ORCA_ERR_CHECK 6         /* a checked step found a broken invariant */
 
 /* largest max_neighbors the kernels are compiled for */
 #define ORCA_MAX_NEIGHBORS 32
@@ -81,6 +82,16 @@ extern "C" {
    results agree with the incremental LP to FP32 rounding.  One LP-scheme
    flag at a time. */
 #define ORCA_FLAG_LP_WARP 16u
+/* Checked mode: every step certifies its own results on the device and
+   records ORCA_ERR_CHECK (read by orca_scene_sync_status) when one fails:
+   each neighbour list is sorted by (d^2, index), within R_n, without the
+   agent itself; the agent lies in its slot's cell range; the new velocity is
+   finite, inside the speed disc and, when the half-planes are feasible,
+   inside every one of them (else its largest penetration is t*); the new
+   position is finite (all up to FP32 rounding).  The results agree with the
+   plain step to FP32 rounding; the checks cost time.  Not with an LP-scheme
+   flag. */
+#define ORCA_DEBUG_CHECKED 32u
 
 /*
  * Global parameters of one scene (Sec. 3 and 3.1).
@@ -97,8 +108,8 @@ extern "C" {
  *   origin_x/y, grid_nx/ny   grid box; agents outside clamp to edge cells
  *   block_size      threads per block of the solve kernel (0 = 128)
  *   debug_flags     ORCA_DEBUG_NONE, or one of ORCA_FLAG_LP_WORK_UNITS,
- *                   ORCA_FLAG_LP_ENUMERATION, ORCA_FLAG_LP_WARP, and/or
- *                   ORCA_DEBUG_BARRIER_TIMEOUT
+ *                   ORCA_FLAG_LP_ENUMERATION, ORCA_FLAG_LP_WARP and
+ *                   ORCA_DEBUG_CHECKED, and/or ORCA_DEBUG_BARRIER_TIMEOUT
  *   vehicle_turn_rate, vehicle_accel   kinematic limits of vehicles (type 1),
  *                   rad/s and m/s^2, 0 = off (default).  The paper names such
  *                   extra linear constraints as its extension for vehicles

@@ -127,7 +127,8 @@ SIGNATURES = {
 NOALLOC_SCRATCH_BYTES = 2 << 20
 
 STATUS = {0: "ORCA_OK", 1: "ORCA_ERR_INVALID_ARG", 2: "ORCA_ERR_CUDA",
-          3: "ORCA_ERR_TIMEOUT", 4: "ORCA_ERR_NONFINITE", 5: "ORCA_ERR_CAPACITY"}
+          3: "ORCA_ERR_TIMEOUT", 4: "ORCA_ERR_NONFINITE", 5: "ORCA_ERR_CAPACITY",
+          6: "ORCA_ERR_CHECK"}
 MAX_NEIGHBORS = 32
 
 

@@ -37,6 +37,7 @@ LP_WORK_UNITS = 2   # orca_params.debug_flags: the paper's work-unit batch LP
 BARRIER_TIMEOUT_TEST = 4   # orca_params.debug_flags: failure-detection test hook
 LP_ENUMERATION = 8   # orca_params.debug_flags: active-set enumeration LP (comparison)
 LP_WARP = 16   # orca_params.debug_flags: warp-cooperative LP (comparison)
+CHECKED = 32   # orca_params.debug_flags: steps certify their results on the device
 
 
 def make_params(p, cell_size: float | None = None, block_size: int = 0,

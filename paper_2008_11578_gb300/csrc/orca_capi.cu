@@ -124,8 +124,8 @@ int check_params(const orca_params* p) {
         return ORCA_ERR_CAPACITY;
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 128 || p->block_size % 32))
         return ORCA_ERR_INVALID_ARG;
-    const unsigned schemes =
-        ORCA_FLAG_LP_WORK_UNITS | ORCA_FLAG_LP_ENUMERATION | ORCA_FLAG_LP_WARP;
+    const unsigned schemes = ORCA_FLAG_LP_WORK_UNITS | ORCA_FLAG_LP_ENUMERATION |
+                             ORCA_FLAG_LP_WARP | ORCA_DEBUG_CHECKED;
     if (p->debug_flags & ~(schemes | ORCA_DEBUG_BARRIER_TIMEOUT)) return ORCA_ERR_INVALID_ARG;
     const unsigned scheme = p->debug_flags & schemes;
     if (scheme & (scheme - 1u)) return ORCA_ERR_INVALID_ARG;   // one LP scheme at a time
@@ -226,6 +226,9 @@ cudaError_t prepare_solve(size_t smem) {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(solve_kernel<SRC, MODE_PLAIN, LP_WARP>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(solve_kernel<SRC, MODE_CHECK>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return e;
 }
 
@@ -233,7 +236,7 @@ template <class SRC>
 void launch_solve(int mode, int grid, int block, size_t smem, cudaStream_t st, int n, SRC src,
                   const float2* pos, const float2* vel, const uint2* aux, const uint32_t* start,
                   AgentIn ain, const float2* vpd, StepOut out, DebugOut dbg,
-                  unsigned long long* counters, const int* err) {
+                  unsigned long long* counters, int* err) {
 #define ORCA_SOLVE(M, W)                                                                    \
     solve_kernel<SRC, M, W><<<grid, block, smem, st>>>(n, src, pos, vel, aux, start, ain, vpd, \
                                                         out, dbg, counters, err)
@@ -242,6 +245,7 @@ void launch_solve(int mode, int grid, int block, size_t smem, cudaStream_t st, i
     else if (mode == MODE_WORK_UNITS) ORCA_SOLVE(MODE_PLAIN, LP_WORK_UNITS);
     else if (mode == MODE_ENUMERATION) ORCA_SOLVE(MODE_PLAIN, LP_ENUMERATION);
     else if (mode == MODE_WARP_LP) ORCA_SOLVE(MODE_PLAIN, LP_WARP);
+    else if (mode == MODE_CHECK) ORCA_SOLVE(MODE_CHECK, LP_INCREMENTAL);
     else ORCA_SOLVE(MODE_PLAIN, LP_INCREMENTAL);
 #undef ORCA_SOLVE
 }
@@ -285,6 +289,7 @@ int step_mode(const Pipeline& P) {
     if (P.dbg.act != nullptr) return MODE_RECORD;
     if (P.flags & ORCA_FLAG_LP_WORK_UNITS) return MODE_WORK_UNITS;
     if (P.flags & ORCA_FLAG_LP_WARP) return MODE_WARP_LP;
+    if (P.flags & ORCA_DEBUG_CHECKED) return MODE_CHECK;
     return (P.flags & ORCA_FLAG_LP_ENUMERATION) ? MODE_ENUMERATION : MODE_PLAIN;
 }
 
@@ -399,6 +404,7 @@ int read_status(const Pipeline& P) {
         return ORCA_ERR_CUDA;
     if (h[0] & ERR_BIT_NONFINITE) return ORCA_ERR_NONFINITE;
     if (h[0] & (ERR_BIT_TIMEOUT | ERR_BIT_STATE)) return ORCA_ERR_TIMEOUT;
+    if (h[0] & ERR_BIT_CHECK) return ORCA_ERR_CHECK;
     return ORCA_OK;
 }
 
@@ -643,11 +649,12 @@ const char* orca_status_string(int status) {
         case ORCA_ERR_TIMEOUT: return "bounded device wait timed out";
         case ORCA_ERR_NONFINITE: return "non-finite position or velocity";
         case ORCA_ERR_CAPACITY: return "capacity exceeded";
+        case ORCA_ERR_CHECK: return "checked step: invariant violated";
         default: return "unknown status";
     }
 }
 
-int orca_abi_version(void) { return 3; }
+int orca_abi_version(void) { return 4; }
 
 int orca_workspace_bytes(const orca_params* params, int n_agents, size_t* out_bytes) {
     int st = check_params(params);
@@ -1191,6 +1198,7 @@ extern "C" int orca_step_noalloc(const orca_params* params, const orca_agents* a
             return ORCA_ERR_CUDA;
         if (h[0] & ERR_BIT_NONFINITE) return ORCA_ERR_NONFINITE;
         if (h[0] & (ERR_BIT_TIMEOUT | ERR_BIT_STATE)) return ORCA_ERR_TIMEOUT;
+        if (h[0] & ERR_BIT_CHECK) return ORCA_ERR_CHECK;
     }
     return ORCA_OK;
 }

@@ -116,8 +116,9 @@ struct DebugOut {
     uint32_t* act;
 };
 
-// Variants of the solve kernel: plain, with work tallies, with the active set
-constexpr int MODE_PLAIN = 0, MODE_COUNT = 1, MODE_RECORD = 2;
+// Variants of the solve kernel: plain, with work tallies, with the active set,
+// and the checked step (plain plus on-device certificates of its results)
+constexpr int MODE_PLAIN = 0, MODE_COUNT = 1, MODE_RECORD = 2, MODE_CHECK = 6;
 // host-side choice of the plain variant with the paper's work-unit LP, or
 // with active-set enumeration
 constexpr int MODE_WORK_UNITS = 3, MODE_ENUMERATION = 4, MODE_WARP_LP = 5;
@@ -133,7 +134,8 @@ constexpr int kNumCounters = 5;
 // Device error word bits.  ERR_BIT_STATE: the binning kernel found cell
 // counts that do not sum to the agent count (reported as a timeout: the only
 // in-library cause is a step cut short by a barrier that gave up).
-enum : int { ERR_BIT_NONFINITE = 1, ERR_BIT_TIMEOUT = 2, ERR_BIT_STATE = 4 };
+// ERR_BIT_CHECK: a checked step (MODE_CHECK) found a broken invariant.
+enum : int { ERR_BIT_NONFINITE = 1, ERR_BIT_TIMEOUT = 2, ERR_BIT_STATE = 4, ERR_BIT_CHECK = 8 };
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;

@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(128)
 solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __restrict__ vel,
              const uint2* __restrict__ aux, const uint32_t* __restrict__ cstart,
              AgentIn ain, const float2* __restrict__ vpd, StepOut out, DebugOut dbg,
-             unsigned long long* __restrict__ counters, const int* __restrict__ err) {
+             unsigned long long* __restrict__ counters, int* __restrict__ err) {
     extern __shared__ float4 smem_lines[];
     // after a binning kernel that gave up or found inconsistent counts the
     // sorted state is not valid: leave everything as it is (the status call
@@ -656,6 +656,24 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         }
     }
 
+    if (MODE == MODE_CHECK && active) {
+        // the k-list: sorted by (d^2, original index), within R_n, no self;
+        // and this agent inside the slot range of its own cell
+        bool bad = cnt > k;
+        unsigned long long prev = 0ull;
+        for (int m = 0; m < cnt; ++m) {
+            const float4 e = L[m * stride];
+            const int j = __float_as_int(e.y);
+            const unsigned long long key =
+                ((unsigned long long)__float_as_uint(e.x) << 32) | __float_as_uint(e.z);
+            bad |= j < 0 || j >= n || j == s || !(e.x < R2) || (m > 0 && key <= prev);
+            prev = key;
+        }
+        const int own = cy * sc.nx + cx;
+        bad |= !((int)__ldg(cs + own) <= s && s < (int)__ldg(cs + own + 1));
+        if (bad) atomicOr(err, ERR_BIT_CHECK);
+    }
+
     // ---- preferred velocity toward the goal or the current waypoint ----
     float2 g = ain.goal[o];
     const float vmax = ain.max_speed[o];
@@ -769,10 +787,28 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
             : solve_velocity(L, stride, nlines, vmax, vpx, vpy, vx, vy, tstar, work, act);
     if (!active) return;
     const uint8_t flags = (uint8_t)(infeasible | (any_overlap ? 4 : 0));
+    if (MODE == MODE_CHECK) {
+        // the LP result: finite, inside the speed disc, and inside every
+        // half-plane (feasible) or at the least penetration t* (fallback),
+        // each up to rounding at the scale of the line's data
+        bool bad = !(isfinite(vx) && isfinite(vy)) ||
+                   vx * vx + vy * vy > vmax * vmax * (1.0f + 1e-5f) + 1e-5f;
+        float tmax = -CUDART_INF_F;
+        for (int i = 0; i < nlines; ++i) {
+            const float4 li = L[i * stride];
+            const float pi = penetration(li, vx, vy);
+            const float tol = 1e-4f * (1.0f + vmax + fabsf(li.x) + fabsf(li.y));
+            if (!infeasible) bad |= pi > tol;
+            tmax = fmaxf(tmax, pi - tol);
+        }
+        if (infeasible) bad |= tstar < -1e-4f * (1.0f + vmax) || tmax > tstar;
+        if (bad) atomicOr(err, ERR_BIT_CHECK);
+    }
 
     // ---- integrate ----
     const float2 pn = make_float2(__fadd_rn(p.x, __fmul_rn(sc.dt, vx)),
                                   __fadd_rn(p.y, __fmul_rn(sc.dt, vy)));
+    if (MODE == MODE_CHECK && !(isfinite(pn.x) && isfinite(pn.y))) atomicOr(err, ERR_BIT_CHECK);
     const int w = out.caller_order ? o : s;
     out.vel[w] = make_float2(vx, vy);
     out.pos[w] = pn;

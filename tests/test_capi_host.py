@@ -30,9 +30,10 @@ def test_every_declared_symbol_is_exported():
 
 
 def test_version_and_status_strings():
-    assert api.orca_abi_version() == 3
+    assert api.orca_abi_version() == 4
     assert api.orca_status_string(0) == "ok"
     assert "non-finite" in api.orca_status_string(4)
+    assert "invariant" in api.orca_status_string(6)
     assert api.orca_status_string(99) == "unknown status"
 
 
@@ -55,12 +56,13 @@ def test_workspace_bytes_and_parameter_validation():
                       (dict(max_neighbors=-1), 1), (dict(max_neighbors=33), 5),
                       (dict(grid_nx=0), 1), (dict(grid_nx=1 << 14, grid_ny=1 << 14), 5),
                       (dict(block_size=48), 1), (dict(block_size=256), 1),
-                      (dict(debug_flags=1), 1), (dict(debug_flags=32), 1),
+                      (dict(debug_flags=1), 1), (dict(debug_flags=128), 1),
                       (dict(debug_flags=10), 1), (dict(debug_flags=14), 1),
-                      (dict(debug_flags=18), 1), (dict(debug_flags=24), 1)]:
+                      (dict(debug_flags=18), 1), (dict(debug_flags=24), 1),
+                      (dict(debug_flags=34), 1), (dict(debug_flags=64), 1)]:
         p = _params(**bad)
         assert L.orca_workspace_bytes(ctypes.byref(p), 10, ctypes.byref(out)) == code, bad
-    for good in (2, 4, 6, 8, 12, 16, 20):   # an LP scheme and/or the barrier-timeout test hook
+    for good in (2, 4, 6, 8, 12, 16, 20, 32, 36):   # one scheme/checked flag, and/or the test hook
         p = _params(debug_flags=good)
         assert L.orca_workspace_bytes(ctypes.byref(p), 10, ctypes.byref(out)) == 0, good
     p = _params()

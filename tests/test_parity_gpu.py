@@ -315,6 +315,37 @@ def test_enumeration_lp_matches_oracle(name):
         s.pos, s.vel = g["pos"], g["vel"]
 
 
+@pytest.mark.parametrize("name", ["open_square", "clusters", "shared_space", "waypoints",
+                                  "kinematic"])
+def test_checked_mode_certifies_and_changes_nothing(name):
+    """ORCA_DEBUG_CHECKED: every step certifies its k-lists, cell ranges and
+    LP results on the device; on correct steps nothing is flagged (over four
+    steps), and one step agrees with the plain step to FP32 rounding (the
+    checked kernel is compiled separately, so multiply-adds may contract
+    differently)."""
+    import torch
+    s = {"open_square": lambda: scenes.open_square(3000, 80.0, seed=63),
+         "clusters": lambda: scenes.clusters(n=62500, side=500.0, n_clusters_axis=2),
+         "shared_space": lambda: scenes.shared_space(n_ped=6400, n_veh=100, side=160.0),
+         "waypoints": lambda: scenes.waypoint_square(n_ped=1500, n_veh=60, side=70.0, seed=9),
+         "kinematic": lambda: scenes.shared_space(n_ped=6400, n_veh=300, side=160.0, seed=8)}[name]()
+    if name == "kinematic":
+        s.params.vehicle_turn_rate, s.params.vehicle_accel = 0.8, 2.0
+    out = {}
+    for flags in (0, api.CHECKED):
+        ds = api.DeviceScene(s, "cuda", flags=flags)
+        ds.step(1)
+        torch.cuda.synchronize()
+        assert ds.sync_status() == 0, flags
+        out[flags] = (ds.pos.cpu().numpy(), ds.vel.cpu().numpy())
+        ds.step(3)
+        torch.cuda.synchronize()
+        assert ds.sync_status() == 0, flags
+        ds.close()
+    assert np.abs(out[0][0].astype(np.float64) - out[api.CHECKED][0]).max() <= 1e-5
+    assert np.abs(out[0][1].astype(np.float64) - out[api.CHECKED][1]).max() <= 1e-5
+
+
 @pytest.mark.parametrize("which", ["shared_space", "waypoints", "clusters"])
 def test_vehicle_kinematic_limits(which):
     """Vehicles with turn-rate and acceleration limits (extra half-planes)
