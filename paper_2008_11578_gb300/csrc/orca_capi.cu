@@ -20,6 +20,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "orca.h"
 #include "orca_adjoint.cuh"
 #include "orca_step_kernels.cuh"
@@ -335,13 +337,18 @@ void enqueue_steps(const Pipeline& P, SRC src, int n_steps, const float* vpref_d
     const int sb = P.block;
     const int sgrid = (n + sb - 1) / sb;
     const size_t smem = solve_smem(P);
+    // NVTX ranges (host side: the enqueue of each step and its two kernels)
+    nvtxRangePushA("orca_step");
     for (int t = 0; t < n_steps; ++t) {
+        nvtxRangePushA("orca_step/binning");
         if (P.bin_begin) cudaEventRecord(P.bin_begin, st);
         // step 0 bins the caller's state; later steps were binned by the
         // previous step's solve kernel
         launch_bin(P, src, t == 0, cur, st);
         cur = 1 - cur;
         if (P.bin_end) cudaEventRecord(P.bin_end, st);
+        nvtxRangePop();
+        nvtxRangePushA("orca_step/solve");
         const float2* vpd =
             vpref_delta ? (const float2*)vpref_delta + (size_t)t * (size_t)n : nullptr;
         if (P.ev_begin) cudaEventRecord(P.ev_begin, st);
@@ -353,7 +360,9 @@ void enqueue_steps(const Pipeline& P, SRC src, int n_steps, const float* vpref_d
         launch_solve(mode, sgrid, sb, smem, st, n, src, B.pos1, B.vel1, B.aux[cur], B.start,
                      ain, vpd, out, dbg_for(t), P.counters, B.err);
         if (P.ev_end) cudaEventRecord(P.ev_end, st);
+        nvtxRangePop();
     }
+    nvtxRangePop();
 }
 
 int run_steps(const Pipeline& P, int n_steps, const float* vpref_delta, cudaStream_t st) {

@@ -546,6 +546,10 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     const float r = aux_rad(as);
     const int ta = aux_type(as);
     const int o = aux_orig(as);
+    if (MODE == MODE_CHECK && o >= n) {   // bounds check of the original index
+        atomicOr(err, ERR_BIT_CHECK);
+        return;
+    }
     const int cx = cell_axis(p.x, sc.origin_x, sc.inv_cell, sc.nx);
     const int cy = cell_axis(p.y, sc.origin_y, sc.inv_cell, sc.ny);
 
@@ -635,6 +639,10 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                 }
                 const int c0 = ry * nx + rx0, c1 = ry * nx + rx1;
                 const int jb = (int)__ldg(cs + c0), je = (int)__ldg(cs + c1 + 1);
+                if (MODE == MODE_CHECK && !(0 <= jb && jb <= je && je <= n)) {
+                    atomicOr(err, ERR_BIT_CHECK);   // bounds check of the run
+                    continue;
+                }
                 n_cand += je - jb;
                 // two candidates per iteration: both position loads in flight
                 for (int j = jb; j < je; j += 2) {
@@ -671,7 +679,10 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         }
         const int own = cy * sc.nx + cx;
         bad |= !((int)__ldg(cs + own) <= s && s < (int)__ldg(cs + own + 1));
-        if (bad) atomicOr(err, ERR_BIT_CHECK);
+        if (bad) {
+            atomicOr(err, ERR_BIT_CHECK);
+            cnt = 0;   // no neighbour access through a list that failed its check
+        }
     }
 
     // ---- preferred velocity toward the goal or the current waypoint ----
@@ -681,6 +692,10 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         const int rt = ain.route[o];
         if (rt >= 0) {
             int wi = ain.wp_idx[o];
+            if (MODE == MODE_CHECK && wi >= ain.n_waypoints) {   // bounds check
+                atomicOr(err, ERR_BIT_CHECK);
+                wi = ain.n_waypoints - 1;
+            }
             if (active && dbg.swp != nullptr) dbg.swp[o] = (uint8_t)wi;
             const float2* W = ain.waypoints + (size_t)rt * ain.n_waypoints;
             float2 w = W[wi];

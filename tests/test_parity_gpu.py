@@ -346,6 +346,33 @@ def test_checked_mode_certifies_and_changes_nothing(name):
     assert np.abs(out[0][1].astype(np.float64) - out[api.CHECKED][1]).max() <= 1e-5
 
 
+def test_save_and_resume_the_state():
+    """The scene state lives in the caller's tensors: saving them
+    (torch.save) and stepping a new scene from the saved copy reproduces the
+    run bit for bit."""
+    import io
+    import torch
+    s = scenes.waypoint_square(n_ped=1500, n_veh=60, side=70.0, seed=9)
+    ds = api.DeviceScene(s, "cuda")
+    ds.step(3)
+    buf = io.BytesIO()
+    torch.save({"pos": ds.pos, "vel": ds.vel, "wp_idx": ds.wp_idx}, buf)
+    ds.step(4)
+    torch.cuda.synchronize()
+    a = [t.cpu().numpy() for t in (ds.pos, ds.vel, ds.wp_idx)]
+    ds.close()
+    buf.seek(0)
+    saved = torch.load(buf)
+    ds2 = api.DeviceScene(s, "cuda")
+    ds2.set_state(pos=saved["pos"], vel=saved["vel"], wp_idx=saved["wp_idx"])
+    ds2.step(4)
+    torch.cuda.synchronize()
+    assert ds2.sync_status() == 0
+    for x, y in zip(a, (ds2.pos, ds2.vel, ds2.wp_idx)):
+        assert np.array_equal(x, y.cpu().numpy())
+    ds2.close()
+
+
 @pytest.mark.parametrize("which", ["shared_space", "waypoints", "clusters"])
 def test_vehicle_kinematic_limits(which):
     """Vehicles with turn-rate and acceleration limits (extra half-planes)
