@@ -361,7 +361,7 @@ def measure_adjoint(dev, n_steps=40, ckpt_every=8, reps=5):
         roll.ds.step(n_steps, d)
         p1.record(stream)
         torch.cuda.synchronize()
-        if r > 0:                                   # the first round is warm-up
+        if r > 0:                                   # the first pass is warm-up
             fw.append(e[0].elapsed_time(e[1]))
             bw.append(e[2].elapsed_time(e[3]))
             plain.append(p0.elapsed_time(p1))

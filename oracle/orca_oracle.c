@@ -22,7 +22,7 @@
  * operation order written below, because both implementations must take the
  * same decisions bit for bit.  Everything continuous is FP64.
  *
- * Readings where the paper is silent (each one is listed in the design doc):
+ * Readings where the paper is silent:
  *   - neighbours: the k nearest candidates with d^2 < R_n^2, ordered by
  *     (d^2, index);
  *   - overlapping pairs use the cut-off-circle construction with tau
