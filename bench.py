@@ -35,15 +35,16 @@ if ROOT not in sys.path:
 
 METRIC = "agent-steps/s"
 
-# Algorithmic FP32 operations per counted item (add/sub/mul/div/sqrt = 1,
-# fused multiply-add = 2), read off the device code of the solve kernel:
-#   candidate key test: 2 sub, 2 mul, 1 add                         =  5
-#   ORCA half-plane: relative state 5, obstacle test 13, cut-off or
-#     leg construction 16-30, leg side filter 9, placement 4       = 50
+# Algorithmic FP32 operations per counted item (add/sub/mul/div/sqrt/compare
+# = 1, fused multiply-add = 2):
+#   candidate key test: 2 sub, 2 mul, 1 add, 1 compare with R_n^2      =  6
+#   ORCA half-plane: relative state, obstacle test, cut-off or leg
+#     construction with one sqrt and one or two divides, leg side
+#     filter, placement (50-64 by branch)                            = 60
 #   LP pair evaluation: 2 determinants, 1 divide, 1 bound           = 10
 #   per agent: preferred velocity 10, disc clip 6, integration 4,
 #     1D set-ups amortised 10                                       = 30
-FLOPS_CAND, FLOPS_LINE, FLOPS_PAIR, FLOPS_AGENT = 5, 50, 10, 30
+FLOPS_CAND, FLOPS_LINE, FLOPS_PAIR, FLOPS_AGENT = 6, 60, 10, 30
 # Algorithmic DRAM bytes of the binning kernel on the first step of a call
 # (the bench times one-step calls, so every timed step is a first step):
 #   cell keys: caller position 8 read, key + slot 8 written, cell counter 8
