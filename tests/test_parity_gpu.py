@@ -166,6 +166,36 @@ def test_k_zero_and_k_32():
         compare(s, g)
 
 
+def test_grid_at_the_cell_limit():
+    """8192 x 8192 = 2^26 cells (ORCA_MAX_CELLS): the binning kernel's scan
+    then runs over 67M counters in the largest per-block ranges; 20,000
+    agents spread over the grid and a dense patch, sampled against the
+    oracle, all cells bit-exact."""
+    s = scenes.open_square(20000, 2048.0, seed=13)
+    rng = np.random.default_rng(13)
+    s.pos[:5000] = (1000.0 + 30.0 * rng.random((5000, 2))).astype(np.float32)   # dense patch
+    cell = 0.25
+    assert s.params.grid_dims(cell) == (8192, 8192)
+    g = gpu_step(s, cell_size=cell)
+    assert g["status"] == 0
+    assert np.array_equal(g["cell"], _cells_oracle(s, cell))
+    sel = np.unique(np.concatenate([np.arange(0, s.n, 13), np.arange(0, 5000, 5)]))
+    compare(s, g, sel=sel)
+
+
+def test_k_32_with_vehicle_kinematic_lines():
+    """The largest shared-memory footprint: k = 32 neighbours plus the three
+    kinematic half-planes of a vehicle (35 slots per thread, opt-in shared
+    memory), blocks of 64 and 128."""
+    s = scenes.shared_space(n_ped=6400, n_veh=300, side=120.0, seed=14)
+    s.params.max_neighbors = 32
+    s.params.vehicle_turn_rate, s.params.vehicle_accel = 0.8, 2.0
+    for block in (64, 128):
+        g = gpu_step(s, block_size=block)
+        assert g["status"] == 0
+        compare(s, g, sel=np.arange(0, s.n, 3))
+
+
 def test_all_agents_in_one_cell_and_outside_box():
     s = scenes.open_square(600, 30.0, seed=11)
     g = gpu_step(s, cell_size=1000.0)
