@@ -212,6 +212,11 @@ int orca_scene_set_debug(orca_scene *scene, int32_t *cell, int32_t *nbr,
  * wp_idx are updated in place.  vpref_delta is NULL or float2[n_steps * N]:
  * an offset added to the preferred velocity of agent i at step t at
  * vpref_delta[t * N + i] (the leaf of the adjoint).
+ * Launches 2 kernels per step (binning, solve).  The last step of a call
+ * also records, in the workspace, the cell order it used; the next call
+ * bins its first step in that order, which only changes memory access
+ * patterns.  Results never depend on it: the caller may change or reorder
+ * any array between calls.
  */
 int orca_step(orca_scene *scene, int n_steps, const float *vpref_delta, void *stream);
 
