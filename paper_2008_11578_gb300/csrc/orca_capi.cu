@@ -1,10 +1,10 @@
 // orca_capi.cu -- the C ABI of liborca (declared in include/orca.h).
 //
 // Host side of the ORCA step: argument validation, workspace layout, and
-// the launch sequence: per call a load kernel and the first step's bin_count,
-// then per step three scan kernels, the scatter and the solve kernel (which
-// bins the new positions for the next step, and writes the last step's
-// results straight into the caller's arrays).
+// the launch sequence: per step one cooperative binning kernel (on a call's
+// first step it reads the caller's arrays) and the solve kernel (which bins
+// the new positions for the next step, and writes the last step's results
+// straight into the caller's arrays).
 //
 // A single scene and a batch of independent scenes run the same kernels.  A
 // batch concatenates its scenes' agents (scene 0 first) and their grid cells

@@ -3,17 +3,18 @@
 // Data layout (device, structure of arrays):
 //   caller order     user pos/vel/goal/radius/max_speed/type/route/wp_idx
 //   "state" order    pos0/vel0: output of the solve kernel, in the cell order
-//                    of the step that produced it (caller order right after
-//                    the load kernel)
+//                    of the step that produced it (on a call's first step
+//                    the binning kernel stages the caller's state here)
 //   sorted order     pos1/vel1 + aux (radius, type, original index): agents
 //                    grouped by grid cell,
 //                    cells in row-major order, scenes one after another
-// One step: cell keys and per-cell slots (bin_count for a call's first step,
-// the previous solve afterwards) -> 3-phase exclusive scan of the cell
-// counts -> scatter into sorted order -> solve (one thread per agent:
-// k-nearest ring search, ORCA lines, LP, integrate) writing pos0/vel0 in
-// sorted order, which becomes the state order of the next step; the last
-// step of a call writes the caller's arrays instead.
+// One step: the binning kernel (cell keys and per-cell slots on a call's
+// first step -- later steps get them from the previous solve -- then the
+// exclusive scan of the cell counts and the scatter into sorted order) ->
+// solve (one thread per agent: k-nearest ring search, ORCA lines, LP,
+// integrate) writing pos0/vel0 in sorted order, which becomes the state
+// order of the next step; the last step of a call writes the caller's
+// arrays instead.
 #pragma once
 
 #include <climits>
@@ -80,12 +81,12 @@ __device__ __forceinline__ int aux_type(uint2 a) { return (int)(a.y >> 31); }
 
 // Where the solve kernel writes the new state.  Ordinary steps write pos/vel
 // in sorted order (the next step's state order) and, when key is set, the
-// next step's cell key and counter slot, which saves that step's bin_count
-// launch.  The last step of a call writes straight to the caller's arrays at
-// the original index instead (caller_order), so no separate kernel has to
-// copy the results back to the caller's order.  It also records the original
-// index of every sorted slot (hint) and raises *hint_ok: the next call bins
-// its agents in that order, which is nearly the new cell order.
+// next step's cell key and counter slot, so that step's binning skips its
+// cell-key phase.  The last step of a call writes straight to the caller's
+// arrays at the original index instead (caller_order), so no separate kernel
+// has to copy the results back to the caller's order.  It also records the
+// original index of every sorted slot (hint) and raises *hint_ok: the next
+// call bins its agents in that order, which is nearly the new cell order.
 struct StepOut {
     float2* pos;
     float2* vel;

@@ -832,7 +832,8 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         if (s == 0) *out.hint_ok = 1;
     }
     if (out.key != nullptr) {
-        // bin the new position for the next step (as bin_count_kernel does)
+        // bin the new position for the next step (as the binning kernel's
+        // cell-key phase does on a call's first step)
         const int ncx = cell_axis(pn.x, sc.origin_x, sc.inv_cell, sc.nx);
         const int ncy = cell_axis(pn.y, sc.origin_y, sc.inv_cell, sc.ny);
         const uint32_t c = (uint32_t)(sc.cell_off + ncy * sc.nx + ncx);
