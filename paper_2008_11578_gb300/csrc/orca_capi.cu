@@ -405,8 +405,10 @@ int read_status(const Pipeline& P) {
     if (cudaDeviceSynchronize() != cudaSuccess) return ORCA_ERR_CUDA;
     int h[4] = {0, 0, 0, 0};
     if (cudaMemcpy(h, P.buf.err, 16, cudaMemcpyDeviceToHost) != cudaSuccess) return ORCA_ERR_CUDA;
-    // clears the status bits and the binning kernel's barrier words; after a
-    // barrier gave up, the cell counts may be left mid-step, so clear them too
+    if (h[0] == 0) return ORCA_OK;   // nothing to clear; the recorded cell order stays
+    // clears the status bits, the recorded cell order and the binning
+    // kernel's barrier words; after a barrier gave up, the cell counts may be
+    // left mid-step, so clear them too
     if (cudaMemset(P.buf.err, 0, 16) != cudaSuccess) return ORCA_ERR_CUDA;
     if ((h[0] & (ERR_BIT_TIMEOUT | ERR_BIT_STATE)) &&
         cudaMemset(P.buf.count, 0, (size_t)P.ncells * 4) != cudaSuccess)
