@@ -67,22 +67,35 @@ def _source_hash():
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic(workload):
-    """DRAM bytes per solve launch from the committed ncu summary, or None
-    when the CUDA sources changed since that capture."""
+def _profiled(workload):
+    """Figures of the committed ncu capture of the solve kernel (DRAM bytes
+    per launch, issue-slot and SIMT utilisation), or {} when the CUDA
+    sources changed since that capture."""
     path = os.path.join(ROOT, "profiles", f"solve_kernel_{workload.split('_', 1)[0]}_1m.md")
     try:
         txt = open(path).read()
     except OSError:
-        return None
+        return {}
+    keys = ("kernel_source_hash", "traffic_bytes_per_launch", "issue_active_pct",
+            "simt_efficiency_pct")
     vals = dict(line.split(": ", 1) for line in txt.splitlines()
-                if line.startswith(("kernel_source_hash: ", "traffic_bytes_per_launch: ")))
+                if line.startswith(tuple(k + ": " for k in keys)))
     if vals.get("kernel_source_hash", "").strip() != _source_hash():
-        return None
-    try:
-        return int(vals["traffic_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+        return {}
+    out = {}
+    for k, conv in (("traffic_bytes_per_launch", int), ("issue_active_pct", float),
+                    ("simt_efficiency_pct", float)):
+        try:
+            out[k] = conv(vals[k])
+        except (KeyError, ValueError):
+            pass
+    return out
+
+
+def _profiled_traffic(workload):
+    """DRAM bytes per solve launch from the committed ncu summary, or None
+    when the CUDA sources changed since that capture."""
+    return _profiled(workload).get("traffic_bytes_per_launch")
 
 
 def _peaks():
@@ -484,12 +497,17 @@ def run_ours(args):
     ds.vel.copy_(saved[1])
     c = counters.cpu().numpy().astype(np.float64)
     flops = FLOPS_CAND * c[0] + FLOPS_LINE * c[1] + FLOPS_PAIR * c[2] + FLOPS_AGENT * c[4]
+    prof = _profiled(args.workload) if args.workload == "clusters_1m" else {}
     solve_avg_s = statistics.mean(solve_ms) / 1e3
     peak_tflops = 2 * FP32_LANES * SMS * SM_MAX_MHZ * 1e6 / 1e12
     achieved = flops / solve_avg_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops,
                 "traffic": _profiled_traffic(args.workload) if args.workload == "clusters_1m" else None,
+                # why the fraction is small (same ncu capture, null when stale):
+                # issue slots busy, and active lanes per issued instruction
+                "ncu_issue_active_pct": prof.get("issue_active_pct"),
+                "ncu_simt_efficiency_pct": prof.get("simt_efficiency_pct"),
                 "kernel": "solve_kernel", "solve_ms": statistics.mean(solve_ms),
                 "solve_share_of_step": statistics.mean(solve_ms) / statistics.mean(step_ms),
                 "flops_per_agent_step": flops / n,

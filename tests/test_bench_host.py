@@ -25,13 +25,18 @@ def test_profiled_traffic_follows_the_source_hash(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h = bench._source_hash()
     prof = tmp_path / "profiles" / "solve_kernel_clusters_1m.md"
-    prof.write_text(f"# x\n\nkernel_source_hash: {h}\ntraffic_bytes_per_launch: 12345\n")
+    prof.write_text(f"# x\n\nkernel_source_hash: {h}\ntraffic_bytes_per_launch: 12345\n"
+                    "issue_active_pct: 70.5\nsimt_efficiency_pct: 27.4\n")
     assert bench._profiled_traffic("clusters_1m") == 12345
+    assert bench._profiled("clusters_1m") == {"traffic_bytes_per_launch": 12345,
+                                              "issue_active_pct": 70.5,
+                                              "simt_efficiency_pct": 27.4}
     # any change of a CUDA source invalidates the captured traffic
     k = tmp_path / "paper_2008_11578_gb300" / "csrc" / "orca_math.cuh"
     k.write_text(k.read_text() + "\n// edited\n")
     assert bench._source_hash() != h
     assert bench._profiled_traffic("clusters_1m") is None
+    assert bench._profiled("clusters_1m") == {}
     # no profile, no traffic
     prof.unlink()
     assert bench._profiled_traffic("clusters_1m") is None
