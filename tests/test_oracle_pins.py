@@ -197,10 +197,62 @@ def test_tstar_three_lines_triangle():
         nrm = np.array([np.cos(th), np.sin(th)])      # admissible direction
         d = np.array([nrm[1], -nrm[0]])               # left normal of d is nrm
         lines.append([*(a * nrm), *d])
-    v, ts, fl, _, _ = oracle.lp(np.array(lines), 3.0, np.array([0.2, 0.1]))
+    v, ts, fl, cond, _ = oracle.lp(np.array(lines), 3.0, np.array([0.2, 0.1]))
     assert fl & 1
     assert abs(ts - a) <= 1e-12
     assert np.abs(v).max() <= 1e-12
+    # all three planes attain t*; any two of them meet at 120 degrees
+    assert abs(cond - 1.0 / math.sin(2 * math.pi / 3)) <= 1e-12
+
+
+# ------------------------------------------- active-set conditioning -------
+# The oracle reports, per agent, the condition number of the active set at
+# its LP result: 1 / sin of the angle between the best-conditioned pair of
+# active boundaries (lines, or a line and the speed circle's tangent), and 1
+# when fewer than two boundaries are active.  The tests use it to decide
+# which agents are ill-conditioned, so its value is pinned by closed forms.
+
+@pytest.mark.parametrize("phi", [math.pi / 6, math.pi / 3, math.pi / 2, 2 * math.pi / 3,
+                                 5 * math.pi / 6])
+def test_active_cond_two_lines_at_a_known_angle(phi):
+    """Two half-planes through the origin whose inward normals n_A, n_B meet
+    at angle phi; v_pref = -(n_A + n_B) lies in the normal cone of the apex,
+    so the result is the apex and the condition number is 1 / sin(phi)."""
+    nA = np.array([0.0, 1.0])
+    nB = np.array([-math.sin(phi), math.cos(phi)])
+    # left normal of d is n: d = (n_y, -n_x)
+    lines = np.array([[0.0, 0.0, nA[1], -nA[0]], [0.0, 0.0, nB[1], -nB[0]]])
+    v, ts, fl, cond, mask = oracle.lp(lines, 3.0, -(nA + nB))
+    assert fl & 1 == 0
+    assert np.abs(v).max() <= 1e-12
+    assert mask == 0b11
+    assert abs(cond - 1.0 / math.sin(phi)) <= 1e-9 / math.sin(phi)
+
+
+@pytest.mark.parametrize("h", [0.25, 1.0, 1.9])
+def test_active_cond_line_against_speed_circle(h):
+    """The half-plane y <= h cut by the speed circle |v| = R: at the corner
+    v* = (sqrt(R^2 - h^2), h) the line's direction makes an angle with the
+    circle's tangent whose sine is |d . v*| / R, so the condition number is
+    R / sqrt(R^2 - h^2).  v_pref = v* + (0, 1) + v*/R has positive
+    multipliers on both boundaries (KKT), so v* is the projection."""
+    R = 2.0
+    vs = np.array([math.sqrt(R * R - h * h), h])
+    lines = np.array([[0.0, h, -1.0, 0.0]])          # admissible side: y <= h
+    v, ts, fl, cond, mask = oracle.lp(lines, R, vs + np.array([0.0, 1.0]) + vs / R)
+    assert fl & 1 == 0
+    assert np.abs(v - vs).max() <= 1e-12
+    assert fl & 8                                      # on the speed circle
+    assert abs(cond - R / math.sqrt(R * R - h * h)) <= 1e-9 * cond
+
+
+def test_active_cond_single_boundary_is_one():
+    """One active line inside the disc, or the circle alone: cond = 1."""
+    lines = np.array([[0.0, 0.5, -1.0, 0.0]])         # y <= 0.5
+    v, _, fl, cond, mask = oracle.lp(lines, 3.0, np.array([0.3, 1.0]))
+    assert np.abs(v - [0.3, 0.5]).max() <= 1e-12 and mask == 1 and cond == 1.0
+    v, _, fl, cond, mask = oracle.lp(np.zeros((0, 4)), 1.5, np.array([3.0, 4.0]))
+    assert np.abs(v - [0.9, 1.2]).max() <= 1e-12 and fl & 8 and cond == 1.0
 
 
 # ------------------------------------------------------- ORCA lines ---------
@@ -409,6 +461,44 @@ def test_waypoints_followed_in_order():
     seq = [int(x[0]) for x in [wpi]]
     assert seq[-1] == 2
     assert np.linalg.norm(pos[0] - [0.0, 5.0]) <= 1e-9
+
+
+def _routed_vehicle(wps, wp_idx, r=0.5, vmax=5.0):
+    wps = np.asarray(wps, np.float32).reshape(1, -1, 2)
+    return scenes.Scene(np.array([[0.0, 0.0]], np.float32), np.zeros((1, 2), np.float32),
+                        wps[0, -1:, :].copy(), np.array([r], np.float32),
+                        np.array([vmax], np.float32), np.array([1], np.uint8),
+                        scenes.OrcaParams(), np.array([0], np.int32), wps,
+                        np.array([wp_idx], np.uint8))
+
+
+def test_waypoint_advance_boundary():
+    """The waypoint index advances when the FP32 |wp - p|^2 <= r^2: a vehicle
+    exactly r away advances (and then heads for the next waypoint), one FP32
+    ulp farther it does not (and heads for the current one, capped so as not
+    to overshoot: v_pref = (wp - p) / dt)."""
+    r = oracle.step(_routed_vehicle([[0.5, 0.0], [0.0, 10.0], [20.0, 0.0]], 0))
+    assert r.wp_idx[0] == 1
+    assert np.abs(r.vel[0] - [0.0, 5.0]).max() <= 1e-12
+    x = float(np.nextafter(np.float32(0.5), np.float32(1.0)))
+    assert np.float32(x) * np.float32(x) > np.float32(0.25)
+    r = oracle.step(_routed_vehicle([[x, 0.0], [0.0, 10.0], [20.0, 0.0]], 0))
+    assert r.wp_idx[0] == 0
+    assert np.abs(r.vel[0] - [x / 0.25, 0.0]).max() <= 1e-12
+
+
+def test_waypoint_advances_at_most_once_per_step_and_holds_the_last():
+    """Two waypoints on the agent: one advance per step.  At the last
+    waypoint the index stays, even with the agent on it."""
+    wps = [[0.0, 0.0], [0.0, 0.0], [0.0, 10.0]]
+    r = oracle.step(_routed_vehicle(wps, 0))
+    assert r.wp_idx[0] == 1
+    r = oracle.step(_routed_vehicle(wps, 1))
+    assert r.wp_idx[0] == 2
+    assert np.abs(r.vel[0] - [0.0, 5.0]).max() <= 1e-12
+    r = oracle.step(_routed_vehicle([[5.0, 0.0], [0.0, 0.0]], 1))
+    assert r.wp_idx[0] == 1
+    assert np.abs(r.vel[0]).max() == 0.0
 
 
 # --------------------------------------------------- neighbour sets ---------
