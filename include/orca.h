@@ -102,9 +102,14 @@ extern "C" {
  *                   (0 <= k <= ORCA_MAX_NEIGHBORS)
  *   f[a][b]         responsibility factor f_{A|B} of an agent of type a
  *                   avoiding one of type b (paper default 1/2, 1, 0, 1/2)
- *   cell_size       grid cell edge; any positive value gives identical
- *                   results (the neighbour search is exact), only speed
- *                   changes
+ *   cell_size       grid cell width (along x); any positive value gives
+ *                   identical results (the neighbour search is exact), only
+ *                   speed changes
+ *   cell_height     grid cell height (along y), 0 = cell_size (square
+ *                   cells); also a speed knob only.  Thin, wide cells suit
+ *                   the search: it scans each grid row outward from the
+ *                   agent's x, so the row height sets how far beyond the
+ *                   k-th nearest neighbour it looks
  *   origin_x/y, grid_nx/ny   grid box; agents outside clamp to edge cells
  *   block_size      threads per block of the solve kernel (0 = 128)
  *   debug_flags     ORCA_DEBUG_NONE, or one of ORCA_FLAG_LP_WORK_UNITS,
@@ -137,6 +142,7 @@ typedef struct orca_params {
     unsigned debug_flags;
     float vehicle_turn_rate;
     float vehicle_accel;
+    float cell_height;
 } orca_params;
 
 /*
@@ -238,13 +244,18 @@ int orca_scene_set_bin_events(orca_scene *scene, void *begin, void *end);
 
 /*
  * Work tallies for FLOP accounting, or NULL to stop.  counters is device
- * memory, uint64[5], accumulated (never cleared) by every following step:
+ * memory, uint64[9], accumulated (never cleared) by every following step:
  *   [0] candidate key tests of the neighbour search
  *   [1] ORCA half-planes built
  *   [2] LP pair evaluations (a constraint tested against another inside a
  *       1D sub-problem or a bisector sub-problem)
  *   [3] agents whose half-planes were infeasible
  *   [4] agent updates
+ *   [5] .. [8] thread clock cycles (clock64) summed over agents: neighbour
+ *       search; preferred velocity and half-planes; velocity LP; the whole
+ *       solve thread from the search on.  Shares of [8] give the phase split
+ *       of the solve kernel (time a thread spends in each phase, stalls
+ *       included).
  * A scene with counters set runs a separate, slower kernel variant.
  */
 int orca_scene_set_counters(orca_scene *scene, unsigned long long *counters);
@@ -453,10 +464,13 @@ void orca_batch_destroy(orca_batch *batch);
  * any other allocation.
  *   - Size limit: the call is refused with ORCA_ERR_CAPACITY when
  *     orca_workspace_bytes(params, agents->n_agents) exceeds
- *     ORCA_NOALLOC_SCRATCH_BYTES (about 16,000 agents on a 256 x 256 grid).
+ *     ORCA_NOALLOC_SCRATCH_BYTES (about 22,000 agents on a 256 x 256 grid).
  *   - The first call on a device looks up the scratch area's device address
  *     (once per device, with that device current).  Make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept for the life of the
+ *     process: after cudaDeviceReset (or anything else that destroys the
+ *     device's primary context) it is stale, so do not call this entry
+ *     point on that device again.
  *   - Every call, from every thread and stream, shares the one scratch area
  *     and it keeps the last call's contents; the call clears what has to
  *     start at zero.  Calls that overlap on the GPU race with each other:

@@ -65,7 +65,7 @@ def lib():
             L.oracle_num_threads.restype = ctypes.c_int
             L.oracle_set_num_threads.argtypes = [ctypes.c_int]
             L.oracle_cells.argtypes = [ctypes.c_int, _F, _F, ctypes.c_float,
-                                       ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_int, ctypes.c_int, _I32]
             L.oracle_pair_line.argtypes = [ctypes.c_double] * 13 + [ctypes.c_int, _D]
             L.oracle_lp.argtypes = [ctypes.c_int, _D, ctypes.c_double,
@@ -102,14 +102,19 @@ def set_num_threads(n: int) -> None:
 
 
 def cells(pos, origin, inv_cell, nx, ny) -> np.ndarray:
-    """Cell id cy*nx + cx of every agent (FP32 decision)."""
+    """Cell id cy*nx + cx of every agent (FP32 decision).
+
+    ``inv_cell`` is fl32(1 / cell edge) for square cells, or a pair
+    (fl32(1 / width), fl32(1 / height)) for rectangular ones."""
+    inv = np.atleast_1d(np.asarray(inv_cell, dtype=np.float32))
+    ix, iy = (inv[0], inv[0]) if inv.size == 1 else (inv[0], inv[1])
     pos = np.ascontiguousarray(pos, dtype=np.float32)
     x = np.ascontiguousarray(pos[:, 0])
     y = np.ascontiguousarray(pos[:, 1])
     out = np.empty(pos.shape[0], np.int32)
     lib().oracle_cells(pos.shape[0], _p(x, _F), _p(y, _F), float(origin[0]),
-                       float(origin[1]), float(np.float32(inv_cell)), int(nx),
-                       int(ny), _p(out, _I32))
+                       float(origin[1]), float(ix), float(iy), int(nx), int(ny),
+                       _p(out, _I32))
     return out
 
 

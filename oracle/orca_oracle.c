@@ -445,13 +445,15 @@ void oracle_set_num_threads(int n)
 #endif
 }
 
-/* Cell id cy*nx + cx of each agent (FP32 decision, paper Sec. 1 grid). */
+/* Cell id cy*nx + cx of each agent (FP32 decision, paper Sec. 1 grid).  The
+   paper fixes no cell shape; cells are w x h rectangles, inv_cell_x =
+   fl32(1/w) along x and inv_cell_y = fl32(1/h) along y (square when equal). */
 void oracle_cells(int n, const float *px, const float *py, float ox, float oy,
-                  float inv_cell, int nx, int ny, int32_t *out)
+                  float inv_cell_x, float inv_cell_y, int nx, int ny, int32_t *out)
 {
     for (int i = 0; i < n; ++i) {
-        int32_t cx = cell_axis(px[i], ox, inv_cell, nx);
-        int32_t cy = cell_axis(py[i], oy, inv_cell, ny);
+        int32_t cx = cell_axis(px[i], ox, inv_cell_x, nx);
+        int32_t cy = cell_axis(py[i], oy, inv_cell_y, ny);
         out[i] = cy * nx + cx;
     }
 }

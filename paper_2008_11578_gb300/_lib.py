@@ -70,7 +70,8 @@ class OrcaParams(ctypes.Structure):
                 ("origin_x", ctypes.c_float), ("origin_y", ctypes.c_float),
                 ("grid_nx", ctypes.c_int), ("grid_ny", ctypes.c_int),
                 ("block_size", ctypes.c_int), ("debug_flags", ctypes.c_uint),
-                ("vehicle_turn_rate", ctypes.c_float), ("vehicle_accel", ctypes.c_float)]
+                ("vehicle_turn_rate", ctypes.c_float), ("vehicle_accel", ctypes.c_float),
+                ("cell_height", ctypes.c_float)]
 
 
 class OrcaAgents(ctypes.Structure):

@@ -41,10 +41,13 @@ CHECKED = 32   # orca_params.debug_flags: steps certify their results on the dev
 
 
 def make_params(p, cell_size: float | None = None, block_size: int = 0,
-                flags: int = 0) -> OrcaParams:
-    """orca_params from a :class:`scenes.OrcaParams` (grid from its box)."""
-    c = float(p.cell_size if cell_size is None else cell_size)
-    nx, ny = p.grid_dims(c)
+                flags: int = 0, cell_height: float | None = None) -> OrcaParams:
+    """orca_params from a :class:`scenes.OrcaParams` (grid from its box).
+
+    ``cell_size`` is the cell width; ``cell_height`` its height (None: the
+    width, unless neither is given and the params fix a height)."""
+    c, h = p.cell_dims(cell_size, cell_height)
+    nx, ny = p.grid_dims(cell_size, cell_height)
     f = np.asarray(p.f, dtype=np.float32).reshape(2, 2)
     cp = OrcaParams()
     cp.neighbor_dist = float(p.neighbor_dist)
@@ -55,6 +58,7 @@ def make_params(p, cell_size: float | None = None, block_size: int = 0,
         for b in range(2):
             cp.f[a][b] = float(f[a, b])
     cp.cell_size = c
+    cp.cell_height = h
     cp.origin_x = float(p.origin[0])
     cp.origin_y = float(p.origin[1])
     cp.grid_nx = int(nx)
@@ -119,7 +123,8 @@ def orca_scene_set_bin_events(handle, begin=None, end=None):
 
 
 def orca_scene_set_counters(handle, counters=None):
-    """Accumulate work tallies into ``counters`` (int64[5] on the device)."""
+    """Accumulate work tallies and phase clock cycles into ``counters``
+    (int64[9] on the device; the layout is in orca.h)."""
     check(_lib.load().orca_scene_set_counters(handle, _ptr(counters)), "orca_scene_set_counters")
 
 
@@ -308,7 +313,7 @@ class DeviceScene:
     """
 
     def __init__(self, scene, device="cuda", cell_size=None, block_size=0, debug=False,
-                 flags=0):
+                 flags=0, cell_height=None):
         torch = _torch()
         self.device = torch.device(device)
         self.scene = scene
@@ -330,7 +335,7 @@ class DeviceScene:
             self.route = t(scene.route, torch.int32)
             self.waypoints = t(scene.waypoints.reshape(-1, 2), torch.float32)
             self.wp_idx = t(scene.wp_idx, torch.uint8)
-        self.params = make_params(scene.params, cell_size, block_size, flags)
+        self.params = make_params(scene.params, cell_size, block_size, flags, cell_height)
         self.ws_bytes = orca_workspace_bytes(self.params, self.n)
         self.workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
         a = OrcaAgents()
@@ -425,12 +430,13 @@ class DeviceBatch:
     ``scene_list`` holds :class:`scenes.Scene` objects; their agents are
     concatenated (scene 0 first) into the device tensors ``pos``, ``vel`` ...
     and ``offsets[s]:offsets[s + 1]`` is scene ``s``'s slice.  Routes are
-    re-based onto the concatenated waypoint rows.  ``cell_sizes`` (one per
-    scene, or None for each scene's default) only changes speed, never
-    results.
+    re-based onto the concatenated waypoint rows.  ``cell_sizes`` and
+    ``cell_heights`` (one per scene, or None for each scene's default) only
+    change speed, never results.
     """
 
-    def __init__(self, scene_list, device="cuda", cell_sizes=None, block_size=0, debug=False):
+    def __init__(self, scene_list, device="cuda", cell_sizes=None, block_size=0, debug=False,
+                 cell_heights=None):
         torch = _torch()
         self.device = torch.device(device)
         dev = self.device
@@ -443,8 +449,10 @@ class DeviceBatch:
         self.n = int(self.offsets[-1])
         if cell_sizes is None:
             cell_sizes = [None] * S
-        self.params_list = [make_params(sc.params, c, block_size)
-                            for sc, c in zip(self.scenes, cell_sizes)]
+        if cell_heights is None:
+            cell_heights = [None] * S
+        self.params_list = [make_params(sc.params, c, block_size, 0, h)
+                            for sc, c, h in zip(self.scenes, cell_sizes, cell_heights)]
         self.kmax = max(int(p.max_neighbors) for p in self.params_list)
 
         def cat(get, dtype):

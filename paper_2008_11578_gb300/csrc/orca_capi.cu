@@ -37,7 +37,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // Workspace carve-up (device, caller owned).  The scene table and the scene
 // id of every slot exist only for batches (n_scenes > 0).
 struct Layout {
-    size_t err, count, start, bsum, key, slot, hint, pos0, vel0, pos1, vel1;
+    size_t err, count, start, bsum, key, slot, hint, xrank, pos0, vel0, pos1, vel1;
     size_t aux[2];
     size_t scenes, sid;
     size_t total;
@@ -62,6 +62,7 @@ Layout make_layout(size_t n, size_t ncells, size_t n_scenes) {
     L.key = take(n * 4);
     L.slot = take((n + 1) * 4);   // + the total of the agent scan
     L.hint = take(n * 4);
+    L.xrank = take(n * 8);
     L.pos0 = take(n * 8);
     L.vel0 = take(n * 8);
     L.pos1 = take(n * 8);
@@ -81,6 +82,7 @@ Layout make_layout(size_t n, size_t ncells, size_t n_scenes) {
 struct Buffers {
     int* err;
     uint32_t *count, *start, *bsum, *key, *slot, *hint;
+    uint2* xrank;
     float2 *pos0, *vel0, *pos1, *vel1;
     uint2* aux[2];
     SceneDev* scenes;
@@ -96,6 +98,7 @@ Buffers carve(char* w, const Layout& L, bool batch) {
     b.key = (uint32_t*)(w + L.key);
     b.slot = (uint32_t*)(w + L.slot);
     b.hint = (uint32_t*)(w + L.hint);
+    b.xrank = (uint2*)(w + L.xrank);
     b.pos0 = (float2*)(w + L.pos0);
     b.vel0 = (float2*)(w + L.vel0);
     b.pos1 = (float2*)(w + L.pos1);
@@ -115,6 +118,7 @@ int check_params(const orca_params* p) {
     if (!finite_pos(p->neighbor_dist) || !finite_pos(p->time_horizon) || !finite_pos(p->dt) ||
         !finite_pos(p->cell_size))
         return ORCA_ERR_INVALID_ARG;
+    if (!std::isfinite(p->cell_height) || p->cell_height < 0.0f) return ORCA_ERR_INVALID_ARG;
     if (!std::isfinite(p->origin_x) || !std::isfinite(p->origin_y)) return ORCA_ERR_INVALID_ARG;
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
@@ -156,12 +160,16 @@ int check_agents(const orca_agents* a) {
     return ORCA_OK;
 }
 
-// ring-search margin: computed cell coordinates differ from exact ones by a
-// relative 3u (two roundings and the rounded inverse); 16u of the largest
-// coordinate covers both agents with room to spare
+// row-bound margin of the neighbour search: computed cell coordinates differ
+// from exact ones by a relative 3u (two roundings and the rounded inverse);
+// 16u of the largest coordinate covers both agents with room to spare
 float ring_delta_for(int nx, int ny) {
     double u = std::ldexp(1.0, -24);
     return (float)(16.0 * u * (double)(std::max(nx, ny) + 2));
+}
+
+float cell_height(const orca_params* p) {
+    return p->cell_height > 0.0f ? p->cell_height : p->cell_size;
 }
 
 SceneDev scene_dev(const orca_params* p, int agent_off, int n, int cell_off) {
@@ -173,13 +181,19 @@ SceneDev scene_dev(const orca_params* p, int agent_off, int n, int cell_off) {
     s.ny = p->grid_ny;
     s.origin_x = p->origin_x;
     s.origin_y = p->origin_y;
-    s.cell_size = p->cell_size;
     volatile float one = 1.0f;
-    s.inv_cell = one / p->cell_size;
+    s.cell_w = p->cell_size;
+    s.cell_h = cell_height(p);
+    s.inv_cell_x = one / s.cell_w;
+    s.inv_cell_y = one / s.cell_h;
     s.ring_delta = ring_delta_for(p->grid_nx, p->grid_ny);
     volatile float R = p->neighbor_dist;
     s.R2 = R * R;
     s.k = p->max_neighbors;
+    // seed window w = seed_w / m for an agent whose own cell holds m agents:
+    // 3 rows of height h and width 2w at density m / (cell_w h) hold
+    // 6 w m / cell_w agents, about 1.5 k when seed_w = 1.5 k cell_w / 6
+    s.seed_w = (float)(0.25 * std::max(p->max_neighbors, 1) * (double)s.cell_w);
     s.inv_tau = one / p->time_horizon;
     s.inv_dt = one / p->dt;
     s.dt = p->dt;
@@ -303,7 +317,7 @@ void launch_bin(const Pipeline& P, SRC src, bool first, int cur, cudaStream_t st
     const orca_agents& A = P.agents;
     const BinArgs a{P.n, P.ncells, (const float2*)A.pos, (const float2*)A.vel, A.radius, A.type,
                     B.pos0, B.vel0, B.aux[cur], B.pos0, B.vel0, B.aux[cur], B.key, B.slot,
-                    B.count, B.start, B.bsum,
+                    B.count, B.start, B.bsum, B.xrank,
                     B.pos1, B.vel1, B.aux[1 - cur], B.err, B.hint,
                     (P.flags & ORCA_DEBUG_BARRIER_TIMEOUT) ? 1 : 0};
     const long long work = std::max((long long)P.n, (long long)P.ncells / 4);
@@ -665,7 +679,7 @@ const char* orca_status_string(int status) {
     }
 }
 
-int orca_abi_version(void) { return 4; }
+int orca_abi_version(void) { return 5; }
 
 int orca_workspace_bytes(const orca_params* params, int n_agents, size_t* out_bytes) {
     int st = check_params(params);

@@ -6,11 +6,13 @@
 //                    of the step that produced it (on a call's first step
 //                    the binning kernel stages the caller's state here)
 //   sorted order     pos1/vel1 + aux (radius, type, original index): agents
-//                    grouped by grid cell,
-//                    cells in row-major order, scenes one after another
+//                    grouped by grid cell, cells in row-major order, scenes
+//                    one after another, and inside a cell ordered by x, so
+//                    that every grid row is one run sorted by x
 // One step: the binning kernel (cell keys and per-cell slots on a call's
 // first step -- later steps get them from the previous solve -- then the
-// exclusive scan of the cell counts and the scatter into sorted order) ->
+// exclusive scan of the cell counts, the scatter into cell order and the
+// ordering by x inside every cell) ->
 // solve (one thread per agent: k-nearest ring search, ORCA lines, LP,
 // integrate) writing pos0/vel0 in sorted order, which becomes the state
 // order of the next step; the last step of a call writes the caller's
@@ -30,9 +32,11 @@ struct SceneDev {
     int cell_off;      // first global cell of the scene
     int nx, ny;
     float origin_x, origin_y;
-    float inv_cell;    // fl32(1 / cell_size)
-    float cell_size;
-    float ring_delta;  // cell-rounding margin of the ring search, in cells
+    float inv_cell_x;  // fl32(1 / cell width)
+    float inv_cell_y;  // fl32(1 / cell height)
+    float cell_w, cell_h;
+    float ring_delta;  // cell-rounding margin of the row bounds, in cells
+    float seed_w;      // seed window of the search: seed_w / (agents in own cell), m
     float R2;          // fl32(R_n * R_n)
     int k;
     float inv_tau, inv_dt, dt;
@@ -129,8 +133,11 @@ constexpr int LP_INCREMENTAL = 0, LP_WORK_UNITS = 1, LP_ENUMERATION = 2, LP_WARP
 // Work tallies of the counting variant of the solve kernel:
 // [0] candidate key tests, [1] ORCA lines built, [2] LP pair evaluations
 // (one constraint against another inside a 1D or bisector sub-problem),
-// [3] agents that took the least-penetration fallback, [4] agents.
-constexpr int kNumCounters = 5;
+// [3] agents that took the least-penetration fallback, [4] agents;
+// thread clock cycles (clock64) summed over agents: [5] neighbour search,
+// [6] preferred velocity and half-planes, [7] velocity LP, [8] the whole
+// thread from the search on (the rest is integration and output).
+constexpr int kNumCounters = 9;
 
 // Device error word bits.  ERR_BIT_STATE: the binning kernel found cell
 // counts that do not sum to the agent count (reported as a timeout: the only

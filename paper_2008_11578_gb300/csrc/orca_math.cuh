@@ -21,6 +21,13 @@ __device__ __forceinline__ int cell_axis(float x, float o, float inv, int n) {
     return (int)fl;
 }
 
+// Unsigned key ordered like the float x (negative values reversed, -0 just
+// below +0, NaNs at the ends): the order of agents inside a grid cell.
+__device__ __forceinline__ uint32_t x_order_key(float x) {
+    const uint32_t u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
 // Neighbour key d^2 = fl32(fl32(dx*dx) + fl32(dy*dy)), dx = fl32(xb - xa).
 __device__ __forceinline__ float key_d2(float xa, float ya, float xb, float yb) {
     float dx = __fsub_rn(xb, xa);

@@ -137,13 +137,17 @@ __global__ void scan_add_kernel(uint32_t* __restrict__ start, const uint32_t* __
 }
 
 // ------------------------------------------------------------- binning ----
-// One cooperative launch per step sorts the agents by cell (counting sort):
+// One cooperative launch per step sorts the agents by cell (counting sort),
+// then by x inside every cell:
 //   A  (first step of a call only) cell key and counter slot of every agent,
 //      from the caller's positions: one atomic increment of its cell count;
 //   B  every block sums the counts of its contiguous range of cells;
 //   C  every block adds up the sums of the blocks before it and scans its
 //      range into cell starts, clearing the counts for the next step;
-//   D  every agent's state moves to slot start[cell] + counter slot.
+//   D  every agent's x key and pre-sort index go to slot
+//      start[cell] + counter slot;
+//   E  every slot counts the slots of its cell with a smaller (x key, slot)
+//      and moves its agent's state there.
 // Later steps skip A: the solve kernel bins the new positions as it writes
 // them.  Grid barriers separate the phases.  The cooperative launch keeps
 // every block resident; a barrier that waits longer than about half a second
@@ -176,6 +180,7 @@ struct BinArgs {
     uint32_t* __restrict__ count;
     uint32_t* __restrict__ start;
     uint32_t* __restrict__ bsum;
+    uint2* __restrict__ xrank;         // cell order: (x as an ordered key, pre-sort index)
     float2* __restrict__ pos1;         // sorted state
     float2* __restrict__ vel1;
     uint2* __restrict__ aux1;
@@ -280,8 +285,8 @@ __global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(SRC src, BinArgs a)
                 grp[u] = 0u;
                 if (valid) {
                     const SceneDev& sc = src.get(oi[u]);
-                    const int cx = cell_axis(p[u].x, sc.origin_x, sc.inv_cell, sc.nx);
-                    const int cy = cell_axis(p[u].y, sc.origin_y, sc.inv_cell, sc.ny);
+                    const int cx = cell_axis(p[u].x, sc.origin_x, sc.inv_cell_x, sc.nx);
+                    const int cy = cell_axis(p[u].y, sc.origin_y, sc.inv_cell_y, sc.ny);
                     c[u] = (uint32_t)(sc.cell_off + cy * sc.nx + cx);
                     grp[u] = __match_any_sync(vm, c[u]);
                 }
@@ -384,46 +389,94 @@ __global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(SRC src, BinArgs a)
     }
     if (!grid_barrier(bar, a.err)) return;
 
-    // ---- D: scatter the state to sorted slots ----
+    // ---- D: cell order: every agent's x key and pre-sort index to its slot ----
     bool lost = false;
     const float2* __restrict__ spos = FIRST ? a.stage_pos : a.pos0;
     const float2* __restrict__ svel = FIRST ? a.stage_vel : a.vel0;
     const uint2* __restrict__ saux = FIRST ? a.stage_aux : a.aux0;
     for (int i0 = gt; i0 < a.n; i0 += kBinUnroll * gs) {
         uint32_t d[kBinUnroll];
+        float x[kBinUnroll];
 #pragma unroll
         for (int u = 0; u < kBinUnroll; ++u) {
             const int i = i0 + u * gs;
             d[u] = 0xffffffffu;
             if (i < a.n) {
                 const uint32_t c = a.key[i];
-                if (c < (uint32_t)a.ncells) d[u] = __ldcg(a.start + c) + a.slot[i];
-            }
-        }
-        float2 p[kBinUnroll], v[kBinUnroll];
-        uint2 x[kBinUnroll];
-#pragma unroll
-        for (int u = 0; u < kBinUnroll; ++u) {
-            const int i = i0 + u * gs;
-            if (i < a.n && d[u] < (uint32_t)a.n) {
                 // staged by this thread in phase A on a first step
-                p[u] = spos[i];
-                v[u] = svel[i];
-                x[u] = saux[i];
+                x[u] = spos[i].x;
+                if (c < (uint32_t)a.ncells) d[u] = __ldcg(a.start + c) + a.slot[i];
             }
         }
 #pragma unroll
         for (int u = 0; u < kBinUnroll; ++u) {
             const int i = i0 + u * gs;
             if (i < a.n) {
-                if (d[u] < (uint32_t)a.n) {
-                    a.pos1[d[u]] = p[u];
-                    a.vel1[d[u]] = v[u];
-                    a.aux1[d[u]] = x[u];
-                } else {
-                    lost = true;
-                }
+                if (d[u] < (uint32_t)a.n) a.xrank[d[u]] = make_uint2(x_order_key(x[u]), (uint32_t)i);
+                else lost = true;
             }
+        }
+    }
+    if (lost) atomicOr(a.err, ERR_BIT_STATE);
+    if (!grid_barrier(bar, a.err)) return;
+
+    // ---- E: inside every cell, order by x (ties by slot); move the state ----
+    // The rank of slot t among the slots of its cell by (x key, slot) is its
+    // place in the cell, so each grid row becomes one run sorted by x, which
+    // the neighbour search scans outward from an agent's x.  O(m) per agent
+    // for a cell of m agents; two slots per thread and four keys per loop
+    // iteration keep several L2 reads in flight.
+    lost = false;
+    for (int t0 = gt; t0 < a.n; t0 += 2 * gs) {
+        uint2 e[2];
+        uint32_t i[2], b[2], en[2], r[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int t = t0 + u * gs;
+            e[u] = t < a.n ? __ldcg(a.xrank + t) : make_uint2(0u, 0xffffffffu);
+            i[u] = e[u].y;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const uint32_t c = i[u] < (uint32_t)a.n ? __ldcg(a.key + i[u]) : 0xffffffffu;
+            b[u] = en[u] = 0u;
+            if (c < (uint32_t)a.ncells) {
+                b[u] = __ldcg(a.start + c);
+                en[u] = __ldcg(a.start + c + 1);
+            } else {
+                lost |= t0 + u * gs < a.n;
+                i[u] = 0xffffffffu;
+            }
+            r[u] = 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const uint32_t t = (uint32_t)(t0 + u * gs), x = e[u].x;
+            uint32_t v = b[u];
+            for (; v + 4 <= en[u]; v += 4) {
+                uint32_t xv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) xv[q] = __ldcg(&a.xrank[v + q].x);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    r[u] += (xv[q] < x || (xv[q] == x && v + q < t)) ? 1u : 0u;
+            }
+            for (; v < en[u]; ++v) {
+                const uint32_t xv = __ldcg(&a.xrank[v].x);
+                r[u] += (xv < x || (xv == x && v < t)) ? 1u : 0u;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (i[u] >= (uint32_t)a.n) continue;
+            const uint32_t dst = b[u] + r[u];
+            if (dst >= (uint32_t)a.n) {
+                lost = true;
+                continue;
+            }
+            a.pos1[dst] = spos[i[u]];
+            a.vel1[dst] = svel[i[u]];
+            a.aux1[dst] = saux[i[u]];
         }
     }
     if (lost) atomicOr(a.err, ERR_BIT_STATE);
@@ -534,6 +587,11 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     const int stride = blockDim.x;
     float4* L = smem_lines + threadIdx.x;
     const int s_raw = blockIdx.x * blockDim.x + threadIdx.x;
+    // A checked step never hands its slot order to the next call: a slot that
+    // fails a bounds check leaves its entry unwritten, so the next call bins
+    // in the caller's order instead (the flag is cleared before any slot can
+    // return early).
+    if (MODE == MODE_CHECK && s_raw == 0 && out.hint_ok != nullptr) *out.hint_ok = 0;
     constexpr bool WORK_UNITS = LP == LP_WORK_UNITS;
     constexpr bool ALL_LANES = WORK_UNITS || LP == LP_WARP;
     if (!ALL_LANES && s_raw >= n) return;
@@ -550,116 +608,195 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         atomicOr(err, ERR_BIT_CHECK);
         return;
     }
-    const int cx = cell_axis(p.x, sc.origin_x, sc.inv_cell, sc.nx);
-    const int cy = cell_axis(p.y, sc.origin_y, sc.inv_cell, sc.ny);
+    const int cx = cell_axis(p.x, sc.origin_x, sc.inv_cell_x, sc.nx);
+    const int cy = cell_axis(p.y, sc.origin_y, sc.inv_cell_y, sc.ny);
+    // the counting variant also records the thread's clock at the phase
+    // boundaries (search, half-planes, LP, the rest)
+    long long clk[4] = {0, 0, 0, 0};
+    if (MODE == MODE_COUNT) clk[0] = clock64();
 
-    // ---- k nearest by (d^2, index), exact ring search over the grid ----
+    // ---- k nearest by (d^2, index), exact search over the x-sorted grid rows ----
     // The list lives in the thread's line slots, sorted ascending by
-    // (d^2, original index): slot m = (d^2, sorted slot j, original index).
-    // An admitted candidate shifts only the entries behind it.
+    // (d^2, original index): slot m = (d^2, sorted slot j, original index or
+    // -1).  The original index only orders equal d^2, so it is read from the
+    // sorted state when a tie needs it (or for the diagnostic outputs), not
+    // for every admitted candidate.  An admitted candidate shifts only the
+    // entries behind it.
     const int k = sc.k;
-    float thr_d = CUDART_INF_F;   // key of the k-th entry once the list is full
-    // (d^2, original index) as one 64-bit key: d^2 >= 0, so its bits order
-    // like the value, and the index breaks ties in the low word
-    unsigned long long thr_key = ~0ull;
+    float thr_d = CUDART_INF_F;   // d^2 of the k-th entry once the list is full
     int cnt = 0;
     int n_cand = 0, work = 0;
     const float R2 = sc.R2;
     const uint32_t* __restrict__ cs = cstart + sc.cell_off;
+    auto orig_of = [&](int j) { return aux_orig(__ldg(aux + j)); };
+    auto entry_orig = [&](float4 e) {
+        const int eo = __float_as_int(e.z);
+        return eo >= 0 ? eo : orig_of(__float_as_int(e.y));
+    };
 
     // candidate j at key distance d2: admitted when within R_n and its
     // (d^2, original index) key is below the k-th; the entries behind it shift
     auto consider = [&](int j, float d2) {
         if (d2 < R2 && d2 <= thr_d && j != s) {
-            const int oj = aux_orig(__ldg(aux + j));
-            const unsigned long long key =
-                ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)oj;
-            if (key < thr_key) {
-                int at = min(cnt, k - 1);
-                while (at > 0) {
-                    const float4 e = L[(at - 1) * stride];
-                    const unsigned long long ek =
-                        ((unsigned long long)__float_as_uint(e.x) << 32) | __float_as_uint(e.z);
-                    if (ek < key) break;
-                    L[at * stride] = e;
-                    --at;
-                }
-                L[at * stride] = make_float4(d2, __int_as_float(j), __int_as_float(oj), 0.0f);
-                cnt = min(cnt + 1, k);
-                if (cnt == k) {
-                    const float4 e = L[(k - 1) * stride];
-                    thr_d = e.x;
-                    thr_key =
-                        ((unsigned long long)__float_as_uint(e.x) << 32) | __float_as_uint(e.z);
-                }
+            int oj = -1;
+            if (d2 == thr_d) {   // equal to the k-th d^2: the original index decides
+                oj = orig_of(j);
+                if (oj > entry_orig(L[(k - 1) * stride])) return;
             }
+            int at = min(cnt, k - 1);
+            while (at > 0) {
+                const float4 e = L[(at - 1) * stride];
+                if (e.x < d2) break;
+                if (e.x == d2) {
+                    if (oj < 0) oj = orig_of(j);
+                    if (entry_orig(e) < oj) break;
+                }
+                L[at * stride] = e;
+                --at;
+            }
+            L[at * stride] = make_float4(d2, __int_as_float(j), __int_as_float(oj), 0.0f);
+            cnt = min(cnt + 1, k);
+            if (cnt == k) thr_d = L[(k - 1) * stride].x;
         }
     };
 
-    if (k > 0) {
+    if (k > 0 && isfinite(p.x) && isfinite(p.y)) {   // (a non-finite state is an error)
+        // Every grid row is one run of slots sorted by x (the binning kernel
+        // orders each cell by x, and cells of a row are consecutive in x).
+        // A row is scanned outward from the agent's x with two cursors: the
+        // right one stops at the first candidate right of the agent whose
+        // dx^2 exceeds the current k-th key (or R_n^2), the left one likewise
+        // on the left; every candidate farther along has a larger dx^2, and
+        // d^2 = fl(dx^2 + dy^2) >= dx^2, so none of them can enter the list.
+        // Any start slot is valid (candidates on the wrong side of the agent
+        // never stop a cursor); a good start only saves candidate tests.
+        // Rows are visited nearest first and a side of rows ends when the
+        // row's y gap is beyond the k-th key (or R_n).
+        // A seed pass first scans the agent's row and its two neighbours in
+        // a window |dx| <= w, w sized by the agent's own cell count for about
+        // 1.5 k candidates, so that the list starts from a tight k-th key;
+        // the main pass resumes those rows' cursors without the window.
         const int nx = sc.nx, ny = sc.ny;
-        const int mmax = max(max(cx, nx - 1 - cx), max(cy, ny - 1 - cy));
-        const float prx = __fsub_rn(p.x, sc.origin_x), pry = __fsub_rn(p.y, sc.origin_y);
-        for (int m = 0; m <= mmax; ++m) {
-            // ring m = row cy-m, row cy+m (each one contiguous run of cells)
-            // and the two side cells of every row strictly between them
-            const int x0 = max(cx - m, 0), x1 = min(cx + m, nx - 1);
-            const int ylo = cy - m, yhi = cy + m;
-            const int ya = max(ylo + 1, 0), yb = min(yhi - 1, ny - 1);
-            const int nr = (m == 0) ? 1 : 2 + 2 * max(0, yb - ya + 1);
-            for (int rr = 0; rr < nr; ++rr) {
-                int ry, rx0, rx1;
-                if (rr < 2) {
-                    ry = rr ? yhi : ylo;
-                    if (ry < 0 || ry >= ny) continue;
-                    rx0 = x0;
-                    rx1 = x1;
-                } else {
-                    const int q = rr - 2;
-                    ry = ya + (q >> 1);
-                    rx0 = rx1 = (q & 1) ? cx + m : cx - m;
-                    if (rx0 < 0 || rx0 >= nx) continue;
+        const float ch = sc.cell_h, mg = sc.ring_delta * ch;
+        const float pry = __fsub_rn(p.y, sc.origin_y);
+        // lower bound of dy^2 for every agent binned into row ry (widened by
+        // the cell-rounding margin, open toward the grid edge), with the
+        // 1e-5 relative slack of the key comparison
+        auto row_gap2 = [&](int ry) {
+            const float by0 = ry == 0 ? -CUDART_INF_F : (float)ry * ch - mg;
+            const float by1 = ry == ny - 1 ? CUDART_INF_F : (float)(ry + 1) * ch + mg;
+            const float ey = fmaxf(fmaxf(by0 - pry, pry - by1), 0.0f);
+            return ey * ey * 0.99999f;
+        };
+        // beyond the k-th key or R_n: no agent of that row can enter the list
+        auto row_out = [&](float g2) { return g2 >= R2 || (cnt >= k && g2 > thr_d); };
+        // start slot of row ry: the agent's x interpolated inside the row's
+        // cell of column cx (x-sorted, so agents spread roughly evenly)
+        const float fx = __fmul_rn(__fsub_rn(p.x, sc.origin_x), sc.inv_cell_x) - (float)cx;
+        auto row_start = [&](int c) {
+            const int b = (int)__ldg(cs + c), e = (int)__ldg(cs + c + 1);
+            const int off = (int)(fminf(fmaxf(fx, 0.0f), 1.0f) * (float)(e - b));
+            return min(b + off, e);
+        };
+        // scan [jl .. rb) leftward and [jr .. re) rightward while dx^2 stays
+        // within min(k-th key, w2) and below R_n^2; the cursors are left on
+        // the first candidate not tested
+        auto scan = [&](int& jr, int& jl, int rb, int re, float w2) {
+            bool ron = jr < re, lon = jl >= rb;
+            if (MODE == MODE_CHECK && (rb < 0 || re > n || rb > re)) {
+                atomicOr(err, ERR_BIT_CHECK);   // bounds check of the row
+                ron = lon = false;
+            }
+            while (ron || lon) {
+                float2 qr = make_float2(0.0f, 0.0f), ql = make_float2(0.0f, 0.0f);
+                if (ron) qr = pos[jr];
+                if (lon) ql = pos[jl];
+                const float lim = fminf(thr_d, w2);
+                if (ron) {
+                    const float dx = __fsub_rn(qr.x, p.x);
+                    const float dxx = __fmul_rn(dx, dx);
+                    if (dx > 0.0f && (dxx > lim || dxx >= R2)) {
+                        ron = false;
+                    } else {
+                        const float dy = __fsub_rn(qr.y, p.y);
+                        ++n_cand;
+                        consider(jr, __fadd_rn(dxx, __fmul_rn(dy, dy)));
+                        ron = ++jr < re;
+                    }
                 }
-                if (m > 0) {
-                    // No agent of cells rx0..rx1 of row ry can enter the list
-                    // when the run's box is beyond the k-th key (or R_n).  The
-                    // box is taken relative to the grid origin, like the cell
-                    // assignment, widened by the same cell-rounding margin as
-                    // the ring bound, and unbounded toward the grid edge (agents
-                    // outside the box are clamped into edge cells).
-                    const float cz = sc.cell_size, mg = sc.ring_delta * cz;
-                    const float bx0 = rx0 == 0 ? -CUDART_INF_F : (float)rx0 * cz - mg;
-                    const float bx1 = rx1 == nx - 1 ? CUDART_INF_F : (float)(rx1 + 1) * cz + mg;
-                    const float by0 = ry == 0 ? -CUDART_INF_F : (float)ry * cz - mg;
-                    const float by1 = ry == ny - 1 ? CUDART_INF_F : (float)(ry + 1) * cz + mg;
-                    const float ex = fmaxf(fmaxf(bx0 - prx, prx - bx1), 0.0f);
-                    const float ey = fmaxf(fmaxf(by0 - pry, pry - by1), 0.0f);
-                    const float bd2 = (ex * ex + ey * ey) * 0.99999f;
-                    if (bd2 >= R2 || (cnt >= k && bd2 > thr_d)) continue;
-                }
-                const int c0 = ry * nx + rx0, c1 = ry * nx + rx1;
-                const int jb = (int)__ldg(cs + c0), je = (int)__ldg(cs + c1 + 1);
-                if (MODE == MODE_CHECK && !(0 <= jb && jb <= je && je <= n)) {
-                    atomicOr(err, ERR_BIT_CHECK);   // bounds check of the run
-                    continue;
-                }
-                n_cand += je - jb;
-                // two candidates per iteration: both position loads in flight
-                for (int j = jb; j < je; j += 2) {
-                    const int j1 = min(j + 1, je - 1);
-                    const float2 q0 = pos[j], q1 = pos[j1];
-                    const float d0 = key_d2(p.x, p.y, q0.x, q0.y);
-                    const float d1 = j + 1 < je ? key_d2(p.x, p.y, q1.x, q1.y) : CUDART_INF_F;
-                    consider(j, d0);
-                    consider(j + 1, d1);
+                if (lon) {
+                    const float dx = __fsub_rn(ql.x, p.x);
+                    const float dxx = __fmul_rn(dx, dx);
+                    if (dx < 0.0f && (dxx > lim || dxx >= R2)) {
+                        lon = false;
+                    } else {
+                        const float dy = __fsub_rn(ql.y, p.y);
+                        ++n_cand;
+                        consider(jl, __fadd_rn(dxx, __fmul_rn(dy, dy)));
+                        lon = --jl >= rb;
+                    }
                 }
             }
-            // every agent outside rings 0..m is farther than (m - delta) cells
-            const float D = ((float)m - sc.ring_delta) * sc.cell_size;
-            if (D > 0.0f) {
-                const float D2 = D * D * 0.99999f;
-                if (D2 >= R2) break;
-                if (cnt >= k && thr_d < D2) break;
+        };
+
+        // ---- seed pass: rows cy, cy - 1, cy + 1 within |dx| <= w ----
+        const int own = cy * nx + cx;
+        const int m_own = max((int)__ldg(cs + own + 1) - (int)__ldg(cs + own), 1);
+        const float w = sc.seed_w / (float)m_own;
+        const float w2 = fminf(w * w, R2);
+        int sr[3], sl[3];   // cursors of the seed rows (sl = INT_MIN: not scanned)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int ry = cy + (q == 0 ? 0 : (q == 1 ? -1 : 1));
+            sl[q] = INT_MIN;
+            sr[q] = 0;
+            if (ry < 0 || ry >= ny) continue;
+            if (q > 0) {
+                const float g2 = row_gap2(ry);
+                if (g2 > w2 || row_out(g2)) continue;
+            }
+            const int rb = (int)__ldg(cs + ry * nx), re = (int)__ldg(cs + ry * nx + nx);
+            int jr, jl;
+            if (q == 0) {
+                jr = s + 1;   // the agent's own row: start beside the agent
+                jl = s - 1;
+            } else {
+                jr = row_start(ry * nx + cx);
+                jl = jr - 1;
+            }
+            scan(jr, jl, rb, re, w2);
+            sr[q] = jr;
+            sl[q] = jl;
+        }
+
+        // ---- main pass: rows outward from cy until both sides are out ----
+        // (the seed rows resume their cursors; indices into the cursor
+        // arrays are compile-time constants, so they stay in registers)
+        bool up = true, down = true;   // rows cy + m / cy - m left to visit
+        {
+            int jr = sr[0], jl = sl[0];
+            scan(jr, jl, (int)__ldg(cs + cy * nx), (int)__ldg(cs + cy * nx + nx), CUDART_INF_F);
+        }
+        for (int m = 1; up || down; ++m) {
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                bool& live = side == 0 ? down : up;
+                if (!live) continue;
+                const int ry = side == 0 ? cy - m : cy + m;
+                if (ry < 0 || ry >= ny || row_out(row_gap2(ry))) {
+                    live = false;
+                    continue;
+                }
+                int jr, jl;
+                if (m == 1 && sl[1 + side] != INT_MIN) {
+                    jr = sr[1 + side];
+                    jl = sl[1 + side];
+                } else {
+                    jr = row_start(ry * nx + cx);
+                    jl = jr - 1;
+                }
+                scan(jr, jl, (int)__ldg(cs + ry * nx), (int)__ldg(cs + ry * nx + nx),
+                     CUDART_INF_F);
             }
         }
     }
@@ -672,9 +809,13 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         for (int m = 0; m < cnt; ++m) {
             const float4 e = L[m * stride];
             const int j = __float_as_int(e.y);
+            if (j < 0 || j >= n) {   // no index read through an out-of-range slot
+                bad = true;
+                continue;
+            }
             const unsigned long long key =
-                ((unsigned long long)__float_as_uint(e.x) << 32) | __float_as_uint(e.z);
-            bad |= j < 0 || j >= n || j == s || !(e.x < R2) || (m > 0 && key <= prev);
+                ((unsigned long long)__float_as_uint(e.x) << 32) | (unsigned)entry_orig(e);
+            bad |= j == s || !(e.x < R2) || (m > 0 && key <= prev);
             prev = key;
         }
         const int own = cy * sc.nx + cx;
@@ -684,6 +825,8 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
             cnt = 0;   // no neighbour access through a list that failed its check
         }
     }
+
+    if (MODE == MODE_COUNT) clk[1] = clock64();
 
     // ---- preferred velocity toward the goal or the current waypoint ----
     float2 g = ain.goal[o];
@@ -730,7 +873,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     if (active && dbg.nbr != nullptr) {
         int32_t* nb = dbg.nbr + (size_t)o * dbg.k_stride;
         for (int m = 0; m < dbg.k_stride; ++m)
-            nb[m] = m < cnt ? __float_as_int(L[m * stride].z) : -1;
+            nb[m] = m < cnt ? entry_orig(L[m * stride]) : -1;
     }
     bool any_overlap = false;
     uint32_t capbits = 0u, ovbits = 0u;   // per-line construction (MODE_RECORD)
@@ -788,6 +931,8 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         }
     }
 
+    if (MODE == MODE_COUNT) clk[2] = clock64();
+
     // ---- velocity LP, least-penetration fallback ----
     float vx, vy, tstar;
     uint32_t act = 0u;
@@ -800,6 +945,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         : LP == LP_ENUMERATION
             ? solve_velocity_enumeration(L, stride, nlines, vmax, vpx, vpy, vx, vy, tstar, work)
             : solve_velocity(L, stride, nlines, vmax, vpx, vpy, vx, vy, tstar, work, act);
+    if (MODE == MODE_COUNT) clk[3] = clock64();
     if (!active) return;
     const uint8_t flags = (uint8_t)(infeasible | (any_overlap ? 4 : 0));
     if (MODE == MODE_CHECK) {
@@ -829,13 +975,13 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     out.pos[w] = pn;
     if (out.hint != nullptr) {
         out.hint[s] = (uint32_t)o;
-        if (s == 0) *out.hint_ok = 1;
+        if (s == 0 && MODE != MODE_CHECK) *out.hint_ok = 1;
     }
     if (out.key != nullptr) {
         // bin the new position for the next step (as the binning kernel's
         // cell-key phase does on a call's first step)
-        const int ncx = cell_axis(pn.x, sc.origin_x, sc.inv_cell, sc.nx);
-        const int ncy = cell_axis(pn.y, sc.origin_y, sc.inv_cell, sc.ny);
+        const int ncx = cell_axis(pn.x, sc.origin_x, sc.inv_cell_x, sc.nx);
+        const int ncy = cell_axis(pn.y, sc.origin_y, sc.inv_cell_y, sc.ny);
         const uint32_t c = (uint32_t)(sc.cell_off + ncy * sc.nx + ncx);
         out.key[s] = c;
         out.slot[s] = atomicAdd(out.count + c, 1u);
@@ -855,10 +1001,15 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     }
 
     if (MODE == MODE_COUNT) {
+        const long long end = clock64();
         unsigned long long c[kNumCounters] = {(unsigned long long)n_cand,
                                               (unsigned long long)cnt,
                                               (unsigned long long)work,
-                                              (unsigned long long)(flags & 1), 1ull};
+                                              (unsigned long long)(flags & 1), 1ull,
+                                              (unsigned long long)(clk[1] - clk[0]),
+                                              (unsigned long long)(clk[2] - clk[1]),
+                                              (unsigned long long)(clk[3] - clk[2]),
+                                              (unsigned long long)(end - clk[0])};
 #pragma unroll
         for (int q = 0; q < kNumCounters; ++q) atomicAdd(counters + q, c[q]);
     }

@@ -37,9 +37,11 @@ class OrcaParams:
     time_horizon: float = 5.0
     dt: float = 0.25
     f: tuple = ((0.5, 1.0), (0.0, 0.5))
-    # uniform grid over the scene box; cell size is a tuning knob that never
-    # changes results (the neighbour stencil is exact)
+    # uniform grid over the scene box; cell width and height are tuning knobs
+    # that never change results (the neighbour search is exact); height 0
+    # means square cells
     cell_size: float = 2.0
+    cell_height: float = 0.0
     origin: tuple = (0.0, 0.0)
     extent: tuple = (50.0, 50.0)
     # kinematic limits of vehicles (rad/s, m/s^2); 0 = off.  The paper's
@@ -47,10 +49,21 @@ class OrcaParams:
     vehicle_turn_rate: float = 0.0
     vehicle_accel: float = 0.0
 
-    def grid_dims(self, cell_size: float | None = None) -> tuple[int, int]:
-        c = float(self.cell_size if cell_size is None else cell_size)
-        nx = max(1, int(math.ceil(self.extent[0] / c)))
-        ny = max(1, int(math.ceil(self.extent[1] / c)))
+    def cell_dims(self, cell_size: float | None = None,
+                  cell_height: float | None = None) -> tuple[float, float]:
+        """(width, height) of a grid cell; a height of 0 or None means the
+        width (square cells) unless the params fix a height."""
+        w = float(self.cell_size if cell_size is None else cell_size)
+        h = float(self.cell_height if cell_height is None else cell_height)
+        if cell_size is not None and cell_height is None:
+            h = 0.0
+        return w, (h if h > 0.0 else w)
+
+    def grid_dims(self, cell_size: float | None = None,
+                  cell_height: float | None = None) -> tuple[int, int]:
+        w, h = self.cell_dims(cell_size, cell_height)
+        nx = max(1, int(math.ceil(self.extent[0] / w)))
+        ny = max(1, int(math.ceil(self.extent[1] / h)))
         return nx, ny
 
     def f_array(self) -> np.ndarray:

@@ -24,12 +24,12 @@ def half_ulp(x):
 
 
 def gpu_step(scene, n_steps=1, cell_size=None, block_size=0, vpref_delta=None, debug=True,
-             flags=0):
+             flags=0, cell_height=None):
     """Run the CUDA path on a copy of ``scene``; returns numpy outputs."""
     import torch
     from paper_2008_11578_gb300 import api
     ds = api.DeviceScene(scene, "cuda", cell_size=cell_size, block_size=block_size, debug=debug,
-                         flags=flags)
+                         flags=flags, cell_height=cell_height)
     vpd = None
     if vpref_delta is not None:
         vpd = torch.as_tensor(np.ascontiguousarray(vpref_delta, dtype=np.float32), device="cuda")
@@ -44,6 +44,15 @@ def gpu_step(scene, n_steps=1, cell_size=None, block_size=0, vpref_delta=None, d
             out[k] = v.cpu().numpy()
     ds.close()
     return out
+
+
+def cells_oracle(scene, cell_size=None, cell_height=None):
+    """The oracle's cell of every agent for a w x h grid over the scene box."""
+    p = scene.params
+    w, h = p.cell_dims(cell_size, cell_height)
+    nx, ny = p.grid_dims(cell_size, cell_height)
+    inv = (np.float32(1.0) / np.float32(w), np.float32(1.0) / np.float32(h))
+    return oracle.cells(scene.pos, p.origin, inv, nx, ny)
 
 
 def compare(scene, g, sel=None, r=None, vpref_delta=None):

@@ -263,7 +263,7 @@ def test_adjoint_against_oracle_finite_differences_on_the_workload():
     gW = c["dwp"].reshape(W.shape)
     rng = np.random.default_rng(7)
     comps = []
-    for key, arr, nnz, nany in (("d", c["dvpd"], 24, 6), ("w", gW, 10, 4)):
+    for key, arr, nnz, nany in (("d", c["dvpd"], 120, 20), ("w", gW, 50, 10)):
         # nonzero components, taken along a fixed random order of all indices:
         # the float atomics of the chained VJPs add in a run-dependent order,
         # and a component near the threshold that flips then changes one pick,
@@ -275,7 +275,9 @@ def test_adjoint_against_oracle_finite_differences_on_the_workload():
     report, per_comp = {}, {}
     for h in (1e-3, 1e-5):
         fd, gr, kinks = [], [], 0
-        for key, ix in comps:
+        # every sampled component at the workload's step h = 1e-3; the first
+        # 40 again at h = 1e-5
+        for key, ix in (comps if h == 1e-3 else comps[:40]):
             vals = []
             for sg in (1.0, -1.0):
                 D2, W2 = D.copy(), W.copy()
@@ -292,14 +294,20 @@ def test_adjoint_against_oracle_finite_differences_on_the_workload():
         moving = np.abs(fd) > 1e-6
         per_comp[h] = np.abs(fd - gr)[moving] / np.abs(fd)[moving]
     print("central differences of the oracle (h: compared, kinks, relative error):", report)
-    print("per-component relative errors at h = 1e-5: median %.1e, 90th percentile %.1e"
-          % (np.median(per_comp[1e-5]), np.quantile(per_comp[1e-5], 0.9)))
+    print("kink fraction at h = 1e-3: %.2f of %d sampled components"
+          % (report[1e-3][1] / len(comps), len(comps)))
+    for h in (1e-3, 1e-5):
+        pc = per_comp[h]
+        print("per-component relative errors at h = %g: median %.1e, 90th percentile %.1e, "
+              "max %.1e, within 1e-3: %.2f" % (h, np.median(pc), np.quantile(pc, 0.9),
+                                              pc.max(), (pc <= 1e-3).mean()))
     n3, k3, e3 = report[1e-3]
     n5, k5, e5 = report[1e-5]
     # the step size of the workload statement: the compared gradient within 1e-3
-    assert n3 >= 12 and e3 <= 1e-3, report
+    assert n3 >= 100 and e3 <= 1e-3, report
+    assert np.median(per_comp[1e-3]) <= 1e-3, report
     # at h = 1e-5 a few components whose chain crosses an FP32/FP64 borderline
     # decision (feasibility at t* = 0, a line against the speed circle at a
     # near-corner) differ by percent; the typical component agrees to 1e-3
-    assert n5 >= 30 and np.median(per_comp[1e-5]) <= 1e-3, report
+    assert n5 >= 20 and np.median(per_comp[1e-5]) <= 1e-3, report
     assert (per_comp[1e-5] <= 1e-2).mean() >= 0.75, report

@@ -124,16 +124,17 @@ def test_scene_graph_equals_eager():
 def test_autotuned_shapes_change_nothing():
     import torch
     sl = scenes.batched(n_scenes=16, lo=100, hi=3000, seed=35)
-    res = autotune.tune_batch(sl, alphas=(0.5, 1.0, 2.0), blocks=(64, 128), steps=2)
-    assert len(res.table) == 6 and res.ms_per_step > 0
+    res = autotune.tune_batch(sl, alphas=(0.5, 1.0, 2.0), aspects=(1.0, 4.0), blocks=(64, 128),
+                              steps=2)
+    assert len(res.table) == 12 and res.ms_per_step > 0
     ref = api.DeviceBatch(sl, "cuda")
     ref.step(4)
-    for a, bs, _ in res.table:
-        b = api.DeviceBatch(sl, "cuda", cell_sizes=[a * s.params.cell_size for s in sl],
-                            block_size=bs)
+    for a, asp, bs, _ in res.table:
+        b = api.DeviceBatch(sl, "cuda", cell_sizes=[asp * a * s.params.cell_size for s in sl],
+                            cell_heights=[a * s.params.cell_size for s in sl], block_size=bs)
         b.step(4)
         torch.cuda.synchronize()
-        assert torch.equal(ref.pos, b.pos) and torch.equal(ref.vel, b.vel), (a, bs)
+        assert torch.equal(ref.pos, b.pos) and torch.equal(ref.vel, b.vel), (a, asp, bs)
         b.close()
     ref.close()
 

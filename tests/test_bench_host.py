@@ -40,3 +40,28 @@ def test_profiled_traffic_follows_the_source_hash(tmp_path, monkeypatch):
     # no profile, no traffic
     prof.unlink()
     assert bench._profiled_traffic("clusters_1m") is None
+
+
+def test_parity_stats_of_the_cpu_baseline_leg():
+    """The bench's parity statistics (oracle sample of the timed workload
+    against one GPU step) on CPU: a GPU result equal to the oracle's FP32
+    rounding is exact; a planted velocity error and a swapped neighbour are
+    reported."""
+    import numpy as np
+
+    import oracle
+    from paper_2008_11578_gb300 import scenes
+    s = scenes.open_square(300, 25.0, seed=3)
+    sel = np.arange(0, s.n, 3)
+    r = oracle.step(s, sel=sel)
+    full = oracle.step(s)
+    gpu = dict(pos=full.pos.astype(np.float32), vel=full.vel.astype(np.float32),
+               nbr=full.nbr.copy(), cnt=full.cnt.copy(), flags=full.flags.copy())
+    st = bench._parity_stats(s, r, gpu, sel)
+    assert st["neighbour_lists_bit_exact"] and st["agents"] == len(sel)
+    assert st["max_dv_m_s"] <= 1e-7 and st["max_dp_beyond_half_ulp_m"] <= 1e-9
+    gpu["vel"][sel[4], 1] += 3e-4
+    gpu["nbr"][sel[7], [0, 1]] = gpu["nbr"][sel[7], [1, 0]]
+    st = bench._parity_stats(s, r, gpu, sel)
+    assert not st["neighbour_lists_bit_exact"]
+    assert abs(st["max_dv_m_s"] - 3e-4) <= 1e-6

@@ -30,7 +30,7 @@ def test_every_declared_symbol_is_exported():
 
 
 def test_version_and_status_strings():
-    assert api.orca_abi_version() == 4
+    assert api.orca_abi_version() == 5
     assert api.orca_status_string(0) == "ok"
     assert "non-finite" in api.orca_status_string(4)
     assert "invariant" in api.orca_status_string(6)

@@ -13,20 +13,15 @@ import pytest
 
 import oracle
 from paper_2008_11578_gb300 import api, scenes
-from tests.parity_util import compare
+from tests.parity_util import cells_oracle, compare
 
 pytestmark = pytest.mark.gpu
 
 
-def _cells_oracle(scene, cell_size):
-    p = scene.params
-    nx, ny = p.grid_dims(cell_size)
-    return oracle.cells(scene.pos, p.origin, np.float32(1.0 / np.float32(cell_size)), nx, ny)
-
-
-def _calls(scene, cell_size, block_size, n_calls, n_sample, seed):
+def _calls(scene, cell_size, block_size, n_calls, n_sample, seed, cell_height=None):
     import torch
-    ds = api.DeviceScene(scene, "cuda", cell_size=cell_size, block_size=block_size, debug=True)
+    ds = api.DeviceScene(scene, "cuda", cell_size=cell_size, block_size=block_size, debug=True,
+                         cell_height=cell_height)
     cur = scene.copy()
     rng = np.random.default_rng(seed)
     fallbacks = 0
@@ -38,7 +33,7 @@ def _calls(scene, cell_size, block_size, n_calls, n_sample, seed):
                  **{k: v.cpu().numpy() for k, v in ds.dbg.items()})
         if ds.wp_idx is not None:
             g["wp_idx"] = ds.wp_idx.cpu().numpy()
-        assert np.array_equal(g["cell"], _cells_oracle(cur, cell_size)), t
+        assert np.array_equal(g["cell"], cells_oracle(cur, cell_size, cell_height)), t
         # every sample includes fallback agents (the least-penetration path)
         inf = np.nonzero(g["flags"] & 1)[0]
         sel = rng.choice(scene.n, n_sample, replace=False)

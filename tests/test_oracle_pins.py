@@ -549,6 +549,22 @@ def test_cells_exact_boundaries_and_clamp():
     assert list(oracle.cells(pos2, (0.0, 0.0), inv, 5, 5)) == [5 * c_ for c_ in [0, 0, 0, 1, 1, 2, 4, 4, 4]]
 
 
+def test_rectangular_cells_exact_boundaries_and_clamp():
+    """w x h cells (w = 4, h = 0.5): x uses 1/w and y 1/h, each edge exact,
+    clamped to the grid; the id is cy * nx + cx.  Transposing the roles of
+    the two axes would put (4, 0) in column 8 and (0, 0.5) in row 0."""
+    inv = (np.float32(1.0) / np.float32(4.0), np.float32(1.0) / np.float32(0.5))
+    nx, ny = 3, 8
+    pts = np.array([[0.0, 0.0], [3.999, 0.0], [4.0, 0.0], [0.0, 0.4999], [0.0, 0.5],
+                    [8.0, 1.0], [11.99, 3.75], [12.0, 4.0], [-1.0, -1.0], [100.0, 100.0]],
+                   np.float32)
+    want = [0, 0, 1, 0, nx, 2 + 2 * nx, 2 + 7 * nx, 2 + 7 * nx, 0, 2 + 7 * nx]
+    assert list(oracle.cells(pts, (0.0, 0.0), inv, nx, ny)) == want
+    # an origin shifts both axes: (1 + 4, -2 + 0.5) is cell (1, 1)
+    assert list(oracle.cells(np.array([[5.0, -1.5]], np.float32), (1.0, -2.0), inv, nx, ny)) \
+        == [1 + nx]
+
+
 # ------------------------------------------------------ invariants ----------
 
 def _spawn_non_overlapping(rng, n, side, r=0.5, gap=0.2):

@@ -10,16 +10,10 @@ import pytest
 
 import oracle
 from paper_2008_11578_gb300 import api, scenes
+from tests.parity_util import cells_oracle as _cells_oracle
 from tests.parity_util import compare, gpu_step
 
 pytestmark = pytest.mark.gpu
-
-
-def _cells_oracle(scene, cell_size=None):
-    p = scene.params
-    c = p.cell_size if cell_size is None else cell_size
-    nx, ny = p.grid_dims(c)
-    return oracle.cells(scene.pos, p.origin, np.float32(1.0 / np.float32(c)), nx, ny)
 
 
 def test_open_square_one_step():
@@ -91,14 +85,34 @@ def test_vpref_delta():
 
 
 def test_results_independent_of_cell_and_block_size():
-    """The neighbour search is exact, so the grid and launch shape change
-    nothing: outputs are bitwise identical."""
+    """The neighbour search is exact, so the grid (square or rectangular
+    cells) and launch shape change nothing: outputs are bitwise identical."""
     s = scenes.open_square(1500, 60.0, seed=4)
     ref = gpu_step(s, n_steps=3)
-    for c, b in [(0.7, 0), (5.0, 64), (13.0, 32), (61.0, 96), (2.0, 128)]:
-        g = gpu_step(s, n_steps=3, cell_size=c, block_size=b)
+    for c, h, b in [(0.7, None, 0), (5.0, None, 64), (13.0, None, 32), (61.0, None, 96),
+                    (2.0, None, 128), (4.0, 0.5, 64), (0.5, 4.0, 128), (30.0, 0.25, 64),
+                    (1.0, 61.0, 32)]:
+        g = gpu_step(s, n_steps=3, cell_size=c, cell_height=h, block_size=b)
         assert np.array_equal(g["pos"], ref["pos"]) and np.array_equal(g["vel"], ref["vel"])
         assert np.array_equal(g["nbr"], ref["nbr"])
+        g1 = gpu_step(s, cell_size=c, cell_height=h, block_size=b)   # cells of step 1
+        assert np.array_equal(g1["cell"], _cells_oracle(s, c, h))
+
+
+@pytest.mark.parametrize("w,h", [(4.0, 0.5), (2.0, 0.375), (0.5, 0.5), (8.0, 1.0)])
+def test_rectangular_cells_at_cluster_density(w, h):
+    """Thin, wide cells (the search's preferred shape) at the density of the
+    1M-agent workload: cells and neighbour lists bit-exact, velocities and
+    positions within tolerance, on a sample with every fallback agent."""
+    s = scenes.clusters(n=62500, side=500.0, n_clusters_axis=2)
+    g = gpu_step(s, cell_size=w, cell_height=h, block_size=64)
+    assert g["status"] == 0
+    assert np.array_equal(g["cell"], _cells_oracle(s, w, h))
+    rng = np.random.default_rng(5)
+    inf = np.nonzero(g["flags"] & 1)[0]
+    sel = np.unique(np.concatenate([rng.choice(s.n, 3000, replace=False),
+                                    rng.choice(inf, min(2000, len(inf)), replace=False)]))
+    compare(s, g, sel=sel)
 
 
 def test_multi_step_call_equals_single_steps_and_is_deterministic():
