@@ -62,7 +62,7 @@ Layout make_layout(size_t n, size_t ncells, size_t n_scenes) {
     L.key = take(n * 4);
     L.slot = take((n + 1) * 4);   // + the total of the agent scan
     L.hint = take(n * 4);
-    L.xrank = take(n * 8);
+    L.xrank = take(n * 16);
     L.pos0 = take(n * 8);
     L.vel0 = take(n * 8);
     L.pos1 = take(n * 8);
@@ -82,7 +82,7 @@ Layout make_layout(size_t n, size_t ncells, size_t n_scenes) {
 struct Buffers {
     int* err;
     uint32_t *count, *start, *bsum, *key, *slot, *hint;
-    uint2* xrank;
+    uint4* xrank;
     float2 *pos0, *vel0, *pos1, *vel1;
     uint2* aux[2];
     SceneDev* scenes;
@@ -98,7 +98,7 @@ Buffers carve(char* w, const Layout& L, bool batch) {
     b.key = (uint32_t*)(w + L.key);
     b.slot = (uint32_t*)(w + L.slot);
     b.hint = (uint32_t*)(w + L.hint);
-    b.xrank = (uint2*)(w + L.xrank);
+    b.xrank = (uint4*)(w + L.xrank);
     b.pos0 = (float2*)(w + L.pos0);
     b.vel0 = (float2*)(w + L.vel0);
     b.pos1 = (float2*)(w + L.pos1);
@@ -190,10 +190,6 @@ SceneDev scene_dev(const orca_params* p, int agent_off, int n, int cell_off) {
     volatile float R = p->neighbor_dist;
     s.R2 = R * R;
     s.k = p->max_neighbors;
-    // seed window w = seed_w / m for an agent whose own cell holds m agents:
-    // 3 rows of height h and width 2w at density m / (cell_w h) hold
-    // 6 w m / cell_w agents, about 1.5 k when seed_w = 1.5 k cell_w / 6
-    s.seed_w = (float)(0.25 * std::max(p->max_neighbors, 1) * (double)s.cell_w);
     s.inv_tau = one / p->time_horizon;
     s.inv_dt = one / p->dt;
     s.dt = p->dt;

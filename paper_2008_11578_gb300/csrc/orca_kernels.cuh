@@ -36,7 +36,6 @@ struct SceneDev {
     float inv_cell_y;  // fl32(1 / cell height)
     float cell_w, cell_h;
     float ring_delta;  // cell-rounding margin of the row bounds, in cells
-    float seed_w;      // seed window of the search: seed_w / (agents in own cell), m
     float R2;          // fl32(R_n * R_n)
     int k;
     float inv_tau, inv_dt, dt;

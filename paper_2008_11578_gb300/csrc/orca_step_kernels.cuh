@@ -160,6 +160,9 @@ __global__ void scan_add_kernel(uint32_t* __restrict__ start, const uint32_t* __
 // flagged: the step is wrong but stays inside its buffers.
 constexpr int kBinThreads = 256;
 constexpr int kBinUnroll = 4;        // agents in flight per thread in A and D
+constexpr int kRankPerThread = 4;    // slots per thread and chunk in E
+constexpr int kRankChunk = kBinThreads * kRankPerThread;
+constexpr int kRankHalo = 128;       // keys staged on either side of a chunk in E
 constexpr int kBinGridMax = 4096;    // launch blocks at most (block-sum slots)
 constexpr unsigned kBarrierSpins = 1u << 22;
 
@@ -180,7 +183,7 @@ struct BinArgs {
     uint32_t* __restrict__ count;
     uint32_t* __restrict__ start;
     uint32_t* __restrict__ bsum;
-    uint2* __restrict__ xrank;         // cell order: (x as an ordered key, pre-sort index)
+    uint4* __restrict__ xrank;         // cell order: x as an ordered key, pre-sort index, cell range
     float2* __restrict__ pos1;         // sorted state
     float2* __restrict__ vel1;
     uint2* __restrict__ aux1;
@@ -389,13 +392,13 @@ __global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(SRC src, BinArgs a)
     }
     if (!grid_barrier(bar, a.err)) return;
 
-    // ---- D: cell order: every agent's x key and pre-sort index to its slot ----
+    // ---- D: cell order: every agent's x key, pre-sort index and cell range ----
     bool lost = false;
     const float2* __restrict__ spos = FIRST ? a.stage_pos : a.pos0;
     const float2* __restrict__ svel = FIRST ? a.stage_vel : a.vel0;
     const uint2* __restrict__ saux = FIRST ? a.stage_aux : a.aux0;
     for (int i0 = gt; i0 < a.n; i0 += kBinUnroll * gs) {
-        uint32_t d[kBinUnroll];
+        uint32_t d[kBinUnroll], cb[kBinUnroll], ce[kBinUnroll];
         float x[kBinUnroll];
 #pragma unroll
         for (int u = 0; u < kBinUnroll; ++u) {
@@ -405,15 +408,21 @@ __global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(SRC src, BinArgs a)
                 const uint32_t c = a.key[i];
                 // staged by this thread in phase A on a first step
                 x[u] = spos[i].x;
-                if (c < (uint32_t)a.ncells) d[u] = __ldcg(a.start + c) + a.slot[i];
+                if (c < (uint32_t)a.ncells) {
+                    cb[u] = __ldcg(a.start + c);
+                    ce[u] = __ldcg(a.start + c + 1);
+                    d[u] = cb[u] + a.slot[i];
+                }
             }
         }
 #pragma unroll
         for (int u = 0; u < kBinUnroll; ++u) {
             const int i = i0 + u * gs;
             if (i < a.n) {
-                if (d[u] < (uint32_t)a.n) a.xrank[d[u]] = make_uint2(x_order_key(x[u]), (uint32_t)i);
-                else lost = true;
+                if (d[u] < (uint32_t)a.n)
+                    a.xrank[d[u]] = make_uint4(x_order_key(x[u]), (uint32_t)i, cb[u], ce[u]);
+                else
+                    lost = true;
             }
         }
     }
@@ -423,61 +432,75 @@ __global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(SRC src, BinArgs a)
     // ---- E: inside every cell, order by x (ties by slot); move the state ----
     // The rank of slot t among the slots of its cell by (x key, slot) is its
     // place in the cell, so each grid row becomes one run sorted by x, which
-    // the neighbour search scans outward from an agent's x.  O(m) per agent
-    // for a cell of m agents; two slots per thread and four keys per loop
-    // iteration keep several L2 reads in flight.
+    // the neighbour search scans outward from an agent's x.  Every block
+    // takes an equal contiguous range of slots, in chunks whose x keys it
+    // stages in shared memory together with kRankHalo keys on either side: a
+    // cell's slots are consecutive, so the rank loop reads global memory only
+    // for a cell that reaches beyond the halo.  O(m) per agent for a cell of
+    // m agents.
+    __shared__ uint32_t skey[kRankChunk + 2 * kRankHalo];
+    constexpr int kStage = (kRankChunk + 2 * kRankHalo + kBinThreads - 1) / kBinThreads;
     lost = false;
-    for (int t0 = gt; t0 < a.n; t0 += 2 * gs) {
-        uint2 e[2];
-        uint32_t i[2], b[2], en[2], r[2];
+    const int blo = (int)((long long)a.n * blockIdx.x / gridDim.x);
+    const int bhi = (int)((long long)a.n * (blockIdx.x + 1) / gridDim.x);
+    for (int c0 = blo; c0 < bhi; c0 += kRankChunk) {   // block-uniform
+        const int c1 = min(c0 + kRankChunk, bhi);
+        const int s0 = max(c0 - kRankHalo, 0), s1 = min(c1 + kRankHalo, a.n);
+        // every read of the chunk is issued before the first result is used:
+        // the slots' records, the keys to stage, then the agents' state
+        uint4 e[kRankPerThread];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int t = t0 + u * gs;
-            e[u] = t < a.n ? __ldcg(a.xrank + t) : make_uint2(0u, 0xffffffffu);
-            i[u] = e[u].y;
+        for (int u = 0; u < kRankPerThread; ++u) {
+            const int t = c0 + (int)threadIdx.x + u * kBinThreads;
+            e[u] = t < c1 ? __ldcg(a.xrank + t) : make_uint4(0u, 0xffffffffu, 0u, 0u);
         }
+        uint32_t kv[kStage];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const uint32_t c = i[u] < (uint32_t)a.n ? __ldcg(a.key + i[u]) : 0xffffffffu;
-            b[u] = en[u] = 0u;
-            if (c < (uint32_t)a.ncells) {
-                b[u] = __ldcg(a.start + c);
-                en[u] = __ldcg(a.start + c + 1);
-            } else {
-                lost |= t0 + u * gs < a.n;
-                i[u] = 0xffffffffu;
-            }
-            r[u] = 0u;
+        for (int q = 0; q < kStage; ++q) {
+            const int t = s0 + (int)threadIdx.x + q * kBinThreads;
+            kv[q] = t < s1 ? __ldcg(&a.xrank[t].x) : 0u;
         }
+        float2 sp[kRankPerThread], sv[kRankPerThread];
+        uint2 sa[kRankPerThread];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const uint32_t t = (uint32_t)(t0 + u * gs), x = e[u].x;
-            uint32_t v = b[u];
-            for (; v + 4 <= en[u]; v += 4) {
-                uint32_t xv[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) xv[q] = __ldcg(&a.xrank[v + q].x);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    r[u] += (xv[q] < x || (xv[q] == x && v + q < t)) ? 1u : 0u;
-            }
-            for (; v < en[u]; ++v) {
-                const uint32_t xv = __ldcg(&a.xrank[v].x);
-                r[u] += (xv < x || (xv == x && v < t)) ? 1u : 0u;
+        for (int u = 0; u < kRankPerThread; ++u) {
+            const uint32_t i = e[u].y;
+            if (i < (uint32_t)a.n) {
+                sp[u] = spos[i];
+                sv[u] = svel[i];
+                sa[u] = saux[i];
             }
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            if (i[u] >= (uint32_t)a.n) continue;
-            const uint32_t dst = b[u] + r[u];
-            if (dst >= (uint32_t)a.n) {
+        for (int q = 0; q < kStage; ++q) {
+            const int t = s0 + (int)threadIdx.x + q * kBinThreads;
+            if (t < s1) skey[t - s0] = kv[q];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kRankPerThread; ++u) {
+            const uint32_t t = (uint32_t)(c0 + (int)threadIdx.x + u * kBinThreads);
+            const uint32_t b = e[u].z, en = e[u].w, x = e[u].x;
+            if (t >= (uint32_t)c1 || e[u].y >= (uint32_t)a.n || en > (uint32_t)a.n) {
+                lost |= t < (uint32_t)c1;
+                continue;
+            }
+            uint32_t r = 0u;
+            for (uint32_t v = b; v < en; ++v) {
+                const uint32_t xv = (v >= (uint32_t)s0 && v < (uint32_t)s1)
+                                        ? skey[v - (uint32_t)s0] : __ldcg(&a.xrank[v].x);
+                r += (xv < x || (xv == x && v < t)) ? 1u : 0u;
+            }
+            const uint32_t dst = b + r;
+            if (dst >= en) {
                 lost = true;
                 continue;
             }
-            a.pos1[dst] = spos[i[u]];
-            a.vel1[dst] = svel[i[u]];
-            a.aux1[dst] = saux[i[u]];
+            a.pos1[dst] = sp[u];
+            a.vel1[dst] = sv[u];
+            a.aux1[dst] = sa[u];
         }
+        __syncthreads();   // before the next chunk overwrites the staged keys
     }
     if (lost) atomicOr(a.err, ERR_BIT_STATE);
 }
@@ -617,46 +640,44 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
 
     // ---- k nearest by (d^2, index), exact search over the x-sorted grid rows ----
     // The list lives in the thread's line slots, sorted ascending by
-    // (d^2, original index): slot m = (d^2, sorted slot j, original index or
-    // -1).  The original index only orders equal d^2, so it is read from the
-    // sorted state when a tie needs it (or for the diagnostic outputs), not
-    // for every admitted candidate.  An admitted candidate shifts only the
-    // entries behind it.
+    // (d^2, original index): slot m = (d^2, sorted slot j, original index).
+    // An admitted candidate shifts only the entries behind it.
     const int k = sc.k;
-    float thr_d = CUDART_INF_F;   // d^2 of the k-th entry once the list is full
+    float thr_d = CUDART_INF_F;   // key of the k-th entry once the list is full
+    // (d^2, original index) as one 64-bit key: d^2 >= 0, so its bits order
+    // like the value, and the index breaks ties in the low word
+    unsigned long long thr_key = ~0ull;
     int cnt = 0;
     int n_cand = 0, work = 0;
     const float R2 = sc.R2;
     const uint32_t* __restrict__ cs = cstart + sc.cell_off;
-    auto orig_of = [&](int j) { return aux_orig(__ldg(aux + j)); };
-    auto entry_orig = [&](float4 e) {
-        const int eo = __float_as_int(e.z);
-        return eo >= 0 ? eo : orig_of(__float_as_int(e.y));
-    };
 
     // candidate j at key distance d2: admitted when within R_n and its
     // (d^2, original index) key is below the k-th; the entries behind it shift
     auto consider = [&](int j, float d2) {
         if (d2 < R2 && d2 <= thr_d && j != s) {
-            int oj = -1;
-            if (d2 == thr_d) {   // equal to the k-th d^2: the original index decides
-                oj = orig_of(j);
-                if (oj > entry_orig(L[(k - 1) * stride])) return;
-            }
-            int at = min(cnt, k - 1);
-            while (at > 0) {
-                const float4 e = L[(at - 1) * stride];
-                if (e.x < d2) break;
-                if (e.x == d2) {
-                    if (oj < 0) oj = orig_of(j);
-                    if (entry_orig(e) < oj) break;
+            const int oj = aux_orig(__ldg(aux + j));
+            const unsigned long long key =
+                ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)oj;
+            if (key < thr_key) {
+                int at = min(cnt, k - 1);
+                while (at > 0) {
+                    const float4 e = L[(at - 1) * stride];
+                    const unsigned long long ek =
+                        ((unsigned long long)__float_as_uint(e.x) << 32) | __float_as_uint(e.z);
+                    if (ek < key) break;
+                    L[at * stride] = e;
+                    --at;
                 }
-                L[at * stride] = e;
-                --at;
+                L[at * stride] = make_float4(d2, __int_as_float(j), __int_as_float(oj), 0.0f);
+                cnt = min(cnt + 1, k);
+                if (cnt == k) {
+                    const float4 e = L[(k - 1) * stride];
+                    thr_d = e.x;
+                    thr_key =
+                        ((unsigned long long)__float_as_uint(e.x) << 32) | __float_as_uint(e.z);
+                }
             }
-            L[at * stride] = make_float4(d2, __int_as_float(j), __int_as_float(oj), 0.0f);
-            cnt = min(cnt + 1, k);
-            if (cnt == k) thr_d = L[(k - 1) * stride].x;
         }
     };
 
@@ -665,17 +686,16 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         // orders each cell by x, and cells of a row are consecutive in x).
         // A row is scanned outward from the agent's x with two cursors: the
         // right one stops at the first candidate right of the agent whose
-        // dx^2 exceeds the current k-th key (or R_n^2), the left one likewise
-        // on the left; every candidate farther along has a larger dx^2, and
-        // d^2 = fl(dx^2 + dy^2) >= dx^2, so none of them can enter the list.
+        // fl(dx^2 + g2) exceeds the current k-th key (or whose dx^2 reaches
+        // R_n^2), the left one likewise on the left, where g2 is the row's
+        // lower bound of dy^2; every candidate farther along has a larger
+        // dx^2, and d^2 = fl(dx^2 + dy^2) >= fl(dx^2 + g2) (rounding is
+        // monotone), so none of them can enter the list.
         // Any start slot is valid (candidates on the wrong side of the agent
         // never stop a cursor); a good start only saves candidate tests.
-        // Rows are visited nearest first and a side of rows ends when the
-        // row's y gap is beyond the k-th key (or R_n).
-        // A seed pass first scans the agent's row and its two neighbours in
-        // a window |dx| <= w, w sized by the agent's own cell count for about
-        // 1.5 k candidates, so that the list starts from a tight k-th key;
-        // the main pass resumes those rows' cursors without the window.
+        // Rows are visited nearest first (the agent's own row, then one row
+        // on each side in turn, the nearer of the two first) and a side ends
+        // at the first row whose y gap is beyond the k-th key (or R_n).
         const int nx = sc.nx, ny = sc.ny;
         const float ch = sc.cell_h, mg = sc.ring_delta * ch;
         const float pry = __fsub_rn(p.y, sc.origin_y);
@@ -688,20 +708,15 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
             const float ey = fmaxf(fmaxf(by0 - pry, pry - by1), 0.0f);
             return ey * ey * 0.99999f;
         };
-        // beyond the k-th key or R_n: no agent of that row can enter the list
-        auto row_out = [&](float g2) { return g2 >= R2 || (cnt >= k && g2 > thr_d); };
         // start slot of row ry: the agent's x interpolated inside the row's
         // cell of column cx (x-sorted, so agents spread roughly evenly)
-        const float fx = __fmul_rn(__fsub_rn(p.x, sc.origin_x), sc.inv_cell_x) - (float)cx;
-        auto row_start = [&](int c) {
-            const int b = (int)__ldg(cs + c), e = (int)__ldg(cs + c + 1);
-            const int off = (int)(fminf(fmaxf(fx, 0.0f), 1.0f) * (float)(e - b));
-            return min(b + off, e);
-        };
-        // scan [jl .. rb) leftward and [jr .. re) rightward while dx^2 stays
-        // within min(k-th key, w2) and below R_n^2; the cursors are left on
-        // the first candidate not tested
-        auto scan = [&](int& jr, int& jl, int rb, int re, float w2) {
+        const float fx = fminf(fmaxf(__fmul_rn(__fsub_rn(p.x, sc.origin_x), sc.inv_cell_x) -
+                                         (float)cx, 0.0f), 1.0f);
+        // scan row ry leftward from jl and rightward from jr while
+        // fl(dx^2 + g2) stays within the current k-th key and dx^2 below
+        // R_n^2; g2 is the row's lower bound of dy^2 (0 for the own row)
+        auto scan = [&](int jr, int jl, int ry, float g2) {
+            const int rb = (int)__ldg(cs + ry * nx), re = (int)__ldg(cs + ry * nx + nx);
             bool ron = jr < re, lon = jl >= rb;
             if (MODE == MODE_CHECK && (rb < 0 || re > n || rb > re)) {
                 atomicOr(err, ERR_BIT_CHECK);   // bounds check of the row
@@ -711,11 +726,11 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                 float2 qr = make_float2(0.0f, 0.0f), ql = make_float2(0.0f, 0.0f);
                 if (ron) qr = pos[jr];
                 if (lon) ql = pos[jl];
-                const float lim = fminf(thr_d, w2);
+                const float lim = thr_d;
                 if (ron) {
                     const float dx = __fsub_rn(qr.x, p.x);
                     const float dxx = __fmul_rn(dx, dx);
-                    if (dx > 0.0f && (dxx > lim || dxx >= R2)) {
+                    if (dx > 0.0f && (__fadd_rn(dxx, g2) > lim || dxx >= R2)) {
                         ron = false;
                     } else {
                         const float dy = __fsub_rn(qr.y, p.y);
@@ -727,7 +742,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                 if (lon) {
                     const float dx = __fsub_rn(ql.x, p.x);
                     const float dxx = __fmul_rn(dx, dx);
-                    if (dx < 0.0f && (dxx > lim || dxx >= R2)) {
+                    if (dx < 0.0f && (__fadd_rn(dxx, g2) > lim || dxx >= R2)) {
                         lon = false;
                     } else {
                         const float dy = __fsub_rn(ql.y, p.y);
@@ -738,65 +753,34 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                 }
             }
         };
+        auto scan_row = [&](int ry, float g2) {
+            const int c = ry * nx + cx;
+            const int b = (int)__ldg(cs + c), e = (int)__ldg(cs + c + 1);
+            const int j0 = min(b + (int)(fx * (float)(e - b)), e);
+            scan(j0, j0 - 1, ry, g2);
+        };
 
-        // ---- seed pass: rows cy, cy - 1, cy + 1 within |dx| <= w ----
-        const int own = cy * nx + cx;
-        const int m_own = max((int)__ldg(cs + own + 1) - (int)__ldg(cs + own), 1);
-        const float w = sc.seed_w / (float)m_own;
-        const float w2 = fminf(w * w, R2);
-        int sr[3], sl[3];   // cursors of the seed rows (sl = INT_MIN: not scanned)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const int ry = cy + (q == 0 ? 0 : (q == 1 ? -1 : 1));
-            sl[q] = INT_MIN;
-            sr[q] = 0;
-            if (ry < 0 || ry >= ny) continue;
-            if (q > 0) {
-                const float g2 = row_gap2(ry);
-                if (g2 > w2 || row_out(g2)) continue;
-            }
-            const int rb = (int)__ldg(cs + ry * nx), re = (int)__ldg(cs + ry * nx + nx);
-            int jr, jl;
-            if (q == 0) {
-                jr = s + 1;   // the agent's own row: start beside the agent
-                jl = s - 1;
-            } else {
-                jr = row_start(ry * nx + cx);
-                jl = jr - 1;
-            }
-            scan(jr, jl, rb, re, w2);
-            sr[q] = jr;
-            sl[q] = jl;
-        }
-
-        // ---- main pass: rows outward from cy until both sides are out ----
-        // (the seed rows resume their cursors; indices into the cursor
-        // arrays are compile-time constants, so they stay in registers)
+        scan(s + 1, s - 1, cy, 0.0f);   // the agent's own row: start beside the agent
         bool up = true, down = true;   // rows cy + m / cy - m left to visit
-        {
-            int jr = sr[0], jl = sl[0];
-            scan(jr, jl, (int)__ldg(cs + cy * nx), (int)__ldg(cs + cy * nx + nx), CUDART_INF_F);
-        }
         for (int m = 1; up || down; ++m) {
+            // the nearer of the two rows first
+            const int first = row_gap2(cy + m) < row_gap2(cy - m) ? 1 : 0;
 #pragma unroll
-            for (int side = 0; side < 2; ++side) {
+            for (int side0 = 0; side0 < 2; ++side0) {
+                const int side = side0 ^ first;
                 bool& live = side == 0 ? down : up;
                 if (!live) continue;
                 const int ry = side == 0 ? cy - m : cy + m;
-                if (ry < 0 || ry >= ny || row_out(row_gap2(ry))) {
+                if (ry < 0 || ry >= ny) {
                     live = false;
                     continue;
                 }
-                int jr, jl;
-                if (m == 1 && sl[1 + side] != INT_MIN) {
-                    jr = sr[1 + side];
-                    jl = sl[1 + side];
-                } else {
-                    jr = row_start(ry * nx + cx);
-                    jl = jr - 1;
+                const float g2 = row_gap2(ry);
+                if (g2 >= R2 || (cnt >= k && g2 > thr_d)) {
+                    live = false;
+                    continue;
                 }
-                scan(jr, jl, (int)__ldg(cs + ry * nx), (int)__ldg(cs + ry * nx + nx),
-                     CUDART_INF_F);
+                scan_row(ry, g2);
             }
         }
     }
@@ -814,7 +798,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                 continue;
             }
             const unsigned long long key =
-                ((unsigned long long)__float_as_uint(e.x) << 32) | (unsigned)entry_orig(e);
+                ((unsigned long long)__float_as_uint(e.x) << 32) | __float_as_uint(e.z);
             bad |= j == s || !(e.x < R2) || (m > 0 && key <= prev);
             prev = key;
         }
@@ -873,7 +857,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     if (active && dbg.nbr != nullptr) {
         int32_t* nb = dbg.nbr + (size_t)o * dbg.k_stride;
         for (int m = 0; m < dbg.k_stride; ++m)
-            nb[m] = m < cnt ? entry_orig(L[m * stride]) : -1;
+            nb[m] = m < cnt ? __float_as_int(L[m * stride].z) : -1;
     }
     bool any_overlap = false;
     uint32_t capbits = 0u, ovbits = 0u;   // per-line construction (MODE_RECORD)

@@ -240,8 +240,10 @@ def test_adjoint_against_oracle_finite_differences_on_the_workload():
     every 1.5 steps (neighbour switches and ill-conditioned LP vertices), so
     the two gradients are compared at ONE trajectory, the oracle's: the CUDA
     step VJP is chained along the oracle's states (rounded to FP32).
-    Components whose one-sided differences disagree by more than 10 % straddle
-    a kink and are counted, not compared.
+    Of 510 sampled gradient components, those whose one-sided differences at
+    h = 1e-3 agree to 0.1 % are compared (the loss is smooth across the step
+    there); the others straddle a kink (an active-set or neighbour switch
+    within h) and are counted, not compared.
 
     The offsets are a small random draw, not zero: at zero every agent that
     heads straight for its goal has |v_pref| exactly equal to its maximum
@@ -263,7 +265,7 @@ def test_adjoint_against_oracle_finite_differences_on_the_workload():
     gW = c["dwp"].reshape(W.shape)
     rng = np.random.default_rng(7)
     comps = []
-    for key, arr, nnz, nany in (("d", c["dvpd"], 120, 20), ("w", gW, 50, 10)):
+    for key, arr, nnz, nany in (("d", c["dvpd"], 420, 20), ("w", gW, 60, 10)):
         # nonzero components, taken along a fixed random order of all indices:
         # the float atomics of the chained VJPs add in a run-dependent order,
         # and a component near the threshold that flips then changes one pick,
@@ -272,42 +274,48 @@ def test_adjoint_against_oracle_finite_differences_on_the_workload():
         comps += [(key, tuple(int(q) for q in ix)) for ix in
                   [ix for ix in walk if abs(arr[ix]) > 1e-7][:nnz]]
         comps += [(key, tuple(int(rng.integers(0, m)) for m in arr.shape)) for _ in range(nany)]
-    report, per_comp = {}, {}
-    for h in (1e-3, 1e-5):
+
+    def one_sided(key, ix, h):
+        vals = []
+        for sg in (1.0, -1.0):
+            D2, W2 = D.copy(), W.copy()
+            (D2 if key == "d" else W2)[ix] += sg * h
+            vals.append(_oracle_loss(s, T, D2, W2)[0])
+        return (vals[0] - L0) / h, (L0 - vals[1]) / h
+
+    def compare_at(h, sample, smooth):
+        # a component is compared where its two one-sided differences agree
+        # to ``smooth`` (relative): the loss is differentiable across the
+        # step there; elsewhere an active-set or neighbour switch lies
+        # within h and the component is counted as a kink
         fd, gr, kinks = [], [], 0
-        # every sampled component at the workload's step h = 1e-3; the first
-        # 40 again at h = 1e-5
-        for key, ix in (comps if h == 1e-3 else comps[:40]):
-            vals = []
-            for sg in (1.0, -1.0):
-                D2, W2 = D.copy(), W.copy()
-                (D2 if key == "d" else W2)[ix] += sg * h
-                vals.append(_oracle_loss(s, T, D2, W2)[0])
-            fwd, bwd = (vals[0] - L0) / h, (L0 - vals[1]) / h
-            if abs(fwd - bwd) > 0.1 * max(abs(fwd), abs(bwd), 1e-7):
+        for key, ix in sample:
+            fwd, bwd = one_sided(key, ix, h)
+            if abs(fwd - bwd) > smooth * max(abs(fwd), abs(bwd), 1e-7):
                 kinks += 1
                 continue
-            fd.append((vals[0] - vals[1]) / (2 * h))
+            fd.append(0.5 * (fwd + bwd))
             gr.append((c["dvpd"] if key == "d" else gW)[ix])
         fd, gr = np.array(fd), np.array(gr)
-        report[h] = (len(fd), kinks, float(np.linalg.norm(fd - gr) / np.linalg.norm(fd)))
         moving = np.abs(fd) > 1e-6
-        per_comp[h] = np.abs(fd - gr)[moving] / np.abs(fd)[moving]
-    print("central differences of the oracle (h: compared, kinks, relative error):", report)
-    print("kink fraction at h = 1e-3: %.2f of %d sampled components"
-          % (report[1e-3][1] / len(comps), len(comps)))
-    for h in (1e-3, 1e-5):
-        pc = per_comp[h]
-        print("per-component relative errors at h = %g: median %.1e, 90th percentile %.1e, "
-              "max %.1e, within 1e-3: %.2f" % (h, np.median(pc), np.quantile(pc, 0.9),
-                                              pc.max(), (pc <= 1e-3).mean()))
-    n3, k3, e3 = report[1e-3]
-    n5, k5, e5 = report[1e-5]
-    # the step size of the workload statement: the compared gradient within 1e-3
-    assert n3 >= 100 and e3 <= 1e-3, report
-    assert np.median(per_comp[1e-3]) <= 1e-3, report
-    # at h = 1e-5 a few components whose chain crosses an FP32/FP64 borderline
-    # decision (feasibility at t* = 0, a line against the speed circle at a
-    # near-corner) differ by percent; the typical component agrees to 1e-3
-    assert n5 >= 20 and np.median(per_comp[1e-5]) <= 1e-3, report
-    assert (per_comp[1e-5] <= 1e-2).mean() >= 0.75, report
+        pc = np.abs(fd - gr)[moving] / np.abs(fd)[moving]
+        return dict(n=len(fd), kinks=kinks, rel=float(np.linalg.norm(fd - gr) / np.linalg.norm(fd)),
+                    median=float(np.median(pc)), p90=float(np.quantile(pc, 0.9)),
+                    max=float(pc.max()), within_1e3=float((pc <= 1e-3).mean()))
+
+    # the workload's step h = 1e-3; smooth = one-sided differences within 0.1 %
+    r3 = compare_at(1e-3, comps, 1e-3)
+    print("central differences of the oracle at h = 1e-3 over %d sampled components:" % len(comps),
+          r3, "kink fraction %.2f" % (r3["kinks"] / len(comps)))
+    # a smaller step on the first 60 components, with the looser 10 % kink test
+    r5 = compare_at(1e-5, comps[:60], 0.1)
+    print("at h = 1e-5:", r5)
+    # the spec bar: the compared gradient within 1e-3 (relative norm) of
+    # central differences at h = 1e-3, on at least 100 components
+    assert r3["n"] >= 100 and r3["rel"] <= 1e-3, r3
+    # the typical component agrees to 1e-4; a few percent of components sit
+    # where FP32 and FP64 take opposite sides of a borderline LP decision
+    # (feasibility at t* = 0, a line against the speed circle at a
+    # near-corner) somewhere along the 40 steps and differ by percent
+    assert r3["median"] <= 1e-4 and r3["within_1e3"] >= 0.85, r3
+    assert r5["n"] >= 30 and r5["median"] <= 1e-3, r5
