@@ -464,7 +464,7 @@ void orca_batch_destroy(orca_batch *batch);
  * any other allocation.
  *   - Size limit: the call is refused with ORCA_ERR_CAPACITY when
  *     orca_workspace_bytes(params, agents->n_agents) exceeds
- *     ORCA_NOALLOC_SCRATCH_BYTES (about 22,000 agents on a 256 x 256 grid).
+ *     ORCA_NOALLOC_SCRATCH_BYTES (about 20,000 agents on a 256 x 256 grid).
  *   - The first call on a device looks up the scratch area's device address
  *     (once per device, with that device current).  Make that first call
  *     before any stream capture.  The address is kept for the life of the
