@@ -272,7 +272,12 @@ def _parity_stats(scene, r, gpu, sel):
     half_ulp = 0.5 * (np.nextafter(p32, np.float32(np.inf)) - p32).astype(np.float64)
     dp = np.maximum(np.abs(gpu["pos"][sel].astype(np.float64) - r.pos) - half_ulp, 0.0).max(1)
     ill = r.cond > 1e3
+    w = int(np.argmax(dv)) if len(dv) else 0
+    worst = {"agent": int(sel[w]), "dv_m_s": float(dv[w]), "cond": float(r.cond[w]),
+             "tstar_oracle": float(r.tstar[w]), "flags_oracle": int(r.flags[w]),
+             "flags_gpu": int(gpu["flags"][sel[w]])} if len(dv) else None
     return {"agents": int(len(sel)), "neighbour_lists_bit_exact": bool(nb_same),
+            "worst": worst,
             "max_dv_m_s": float(dv.max(initial=0.0)),
             "p9999_dv_m_s": float(np.quantile(dv, 0.9999)) if len(dv) else 0.0,
             "max_dp_beyond_half_ulp_m": float(dp.max(initial=0.0)),

@@ -301,10 +301,24 @@ __device__ __forceinline__ bool bisector(float4 li, float4 lj, float4& b) {
 // LP in (v, t): when the optimum violates plane i, the new optimum lies on
 // it, where minimising det_i(v) subject to det_j(v) <= det_i(v) (j < i) and
 // the disc is a 2D LP with the linear objective n_i . v.  Writes the point.
+// Plane offsets are taken relative to s, the agent's own velocity:
+// c'_i = det(d_i, P_i - s).  ORCA lines pass near s (through it when
+// f = 0), so these offsets are small and exact where they vanish; offsets
+// relative to the origin would carry |P| times the FP32 rounding, which the
+// bisector of two nearly parallel planes divides by |n_j - n_i| (a vehicle
+// at full speed among pedestrians: ten lines through v_A, 5e-3 apart in
+// angle, put the vertex 1e-3 m/s off).  Points are in ordinary coordinates.
+// In exact arithmetic each sub-problem is non-empty; when rounding makes one
+// look empty (a bisector that misses the disc, or a 1D interval emptier than
+// the allowance) the step keeps its current point, and *fallback is set: the
+// result is then only an upper bound of t*.
 __device__ __forceinline__ float lp3_min_penetration(const float4* __restrict__ L, int stride,
-                                                     int n, float vmax, float& vx, float& vy,
-                                                     int& work, uint32_t& act) {
+                                                     int n, float vmax, float sx, float sy,
+                                                     float& vx, float& vy, int& work,
+                                                     uint32_t& act, bool* fallback = nullptr) {
     const float tol = lp_tol(vmax);
+    // det(d, P - s)
+    auto cof = [&](float4 l) { return l.z * (l.y - sy) - l.w * (l.x - sx); };
     float4 l0 = L[0];
     vx = -l0.w * vmax;
     vy = l0.z * vmax;
@@ -315,36 +329,46 @@ __device__ __forceinline__ float lp3_min_penetration(const float4* __restrict__ 
         if (penetration(li, vx, vy) <= t) continue;
         float nix = -li.w, niy = li.z;   // objective: maximise n_i . v
         float cx = vmax * nix, cy = vmax * niy;
+        const float ci = cof(li);
         uint32_t ai = act_pack(ACT_VERTEX, true, 1, i, 0, 0);
         for (int j = 0; j < i; ++j) {
             ++work;
             const float4 lj = L[j * stride];
-            {
-                // is plane j above plane i at the current point?
-                // (n_j - n_i) . c < c_j - c_i, tested before the bisector is built
-                const float ax = li.w - lj.w, ay = lj.z - li.z;
-                const float beta = (lj.z * lj.y - lj.w * lj.x) - (li.z * li.y - li.w * li.x);
-                if (beta - (ax * cx + ay * cy) <= 0.0f) continue;
+            // is plane j above plane i at the current point?
+            // (n_j - n_i) . (c - s) < c'_j - c'_i, tested before the bisector is built
+            const float ax = li.w - lj.w, ay = lj.z - li.z;   // n_j - n_i
+            const float beta = cof(lj) - ci;
+            if (beta - (ax * (cx - sx) + ay * (cy - sy)) <= 0.0f) continue;
+            // bisector {det_j = det_i}: (n_j - n_i) . (v - s) = c'_j - c'_i, as a
+            // line through its point closest to s, B' relative to s, with
+            // direction e (admissible side det_j <= det_i on its left)
+            const float a2 = ax * ax + ay * ay;
+            if (a2 <= 1e-12f) continue;   // same direction: one plane dominates
+            const float sc = __fdividef(beta, a2);
+            const float inv = rsqrtf(a2);
+            const float bpx = ax * sc, bpy = ay * sc;
+            const float ex = ay * inv, ey = -ax * inv;
+            const float bx = bpx + sx, by = bpy + sy;
+            float dot = bx * ex + by * ey;
+            float disc = dot * dot + vmax * vmax - (bx * bx + by * by);
+            if (disc < -tol * (1.0f + vmax)) {
+                if (fallback) *fallback = true;
+                continue;
             }
-            float4 bj;
-            if (!bisector(li, lj, bj)) continue;
-            float dot = bj.x * bj.z + bj.y * bj.w;
-            float disc = dot * dot + vmax * vmax - (bj.x * bj.x + bj.y * bj.y);
-            if (disc < -tol * (1.0f + vmax)) continue;
             float sq = sqrtf(fmaxf(disc, 0.0f));
             float tl = -dot - sq, tr = -dot + sq;
             int kl = -1, kr = -1;
             bool ok = true;
             for (int jj = 0; jj < j; ++jj) {
                 work += 2;   // a bisector and a 1D bound
-                // plane jj stays below plane i: (n_jj - n_i) . v >= c_jj - c_i,
-                // on bj at v = B + t e: t (a . e) >= (c_jj - c_i) - a . B
+                // plane jj stays below plane i: (n_jj - n_i) . (v - s) >= c'_jj - c'_i,
+                // on the bisector at v = s + B' + t e: t (a . e) >= (c'_jj - c'_i) - a . B'
                 const float4 lk = L[jj * stride];
-                const float ax = li.w - lk.w, ay = lk.z - li.z;   // n_jj - n_i
-                if (ax * ax + ay * ay <= 1e-12f) continue;        // same direction
-                const float beta = (lk.z * lk.y - lk.w * lk.x) - (li.z * li.y - li.w * li.x);
-                const float den = ax * bj.z + ay * bj.w;
-                const float num = beta - (ax * bj.x + ay * bj.y);
+                const float kx = li.w - lk.w, ky = lk.z - li.z;   // n_jj - n_i
+                if (kx * kx + ky * ky <= 1e-12f) continue;        // same direction
+                const float bk = cof(lk) - ci;
+                const float den = kx * ex + ky * ey;
+                const float num = bk - (kx * bpx + ky * bpy);
                 if (den == 0.0f) {
                     if (num > tol) { ok = false; break; }
                     continue;
@@ -359,12 +383,15 @@ __device__ __forceinline__ float lp3_min_penetration(const float4* __restrict__ 
                 }
                 if (tl > tr + tol) { ok = false; break; }
             }
-            if (!ok) continue;   // empty only through rounding: keep the point
-            const bool right = nix * bj.z + niy * bj.w > 0.0f;
+            if (!ok) {   // empty only through rounding: keep the point
+                if (fallback) *fallback = true;
+                continue;
+            }
+            const bool right = nix * ex + niy * ey > 0.0f;
             float tt = right ? tr : tl;
             const int kb = right ? kr : kl;
-            cx = bj.x + tt * bj.z;
-            cy = bj.y + tt * bj.w;
+            cx = bx + tt * ex;
+            cy = by + tt * ey;
             ai = kb >= 0 ? act_pack(ACT_VERTEX, false, 3, i, j, kb)
                          : act_pack(ACT_VERTEX, true, 2, i, j, 0);
         }
@@ -449,23 +476,26 @@ __device__ __forceinline__ bool valley_tie_break(const float4* __restrict__ L, i
 // The velocity of one agent (paper Sec. 3): the admissible velocity closest
 // to v_pref, else the velocity of least penetration.  Lines are consumed in
 // the order given.  Returns 1 when the half-planes were infeasible.
-// The least-penetration LP runs first: when its t* is above 8 tol no
-// velocity is admissible (a successful 2D LP ends at a point that penetrates
-// every line by at most about 2 tol, its emptiness allowances, so t* would
-// be below that, and the FP32 t* of the least-penetration LP is within its
-// own allowances of the exact one), and the 2D LP is skipped.  Otherwise the 2D LP
-// decides as it would alone.  In dense crowds most agents take the first
-// branch, which saves their 2D LP; the results are those of 2D LP first.
+// The least-penetration LP runs first.  Its t* (offsets relative to the
+// agent's velocity) is accurate to well below 0.1 tol, so t* above that,
+// with no rounding fallback in any step, means no velocity is admissible
+// (the definition, t* > 0) and the 2D LP is skipped.  Otherwise the 2D LP
+// decides, its emptiness allowance covering the rounding of exactly
+// feasible problems such as f = 0 half-planes all through the agent's own
+// velocity on the speed circle.  In dense crowds most agents take the first
+// branch, which saves their 2D LP.
 __device__ __forceinline__ int solve_velocity(const float4* __restrict__ L, int stride, int n,
-                                              float vmax, float vpx, float vpy, float& vx,
-                                              float& vy, float& tstar, int& work,
-                                              uint32_t& act) {
+                                              float vmax, float vpx, float vpy, float sx,
+                                              float sy, float& vx, float& vy, float& tstar,
+                                              int& work, uint32_t& act) {
     tstar = 0.0f;
     if (n == 0) return lp2_project(L, stride, n, vmax, vpx, vpy, vx, vy, work, act) == n ? 0 : 1;
     float v3x, v3y;
     uint32_t act3;
-    const float t3 = lp3_min_penetration(L, stride, n, vmax, v3x, v3y, work, act3);
-    if (t3 <= 8.0f * lp_tol(vmax) &&
+    bool fallback = false;
+    const float t3 =
+        lp3_min_penetration(L, stride, n, vmax, sx, sy, v3x, v3y, work, act3, &fallback);
+    if ((t3 <= 0.1f * lp_tol(vmax) || fallback) &&
         lp2_project(L, stride, n, vmax, vpx, vpy, vx, vy, work, act) == n)
         return 0;
     act = act3;
@@ -490,8 +520,10 @@ __device__ __forceinline__ int solve_velocity(const float4* __restrict__ L, int 
 // unit yields one bound of line i's interval, merged with shared-memory
 // atomics; min and max are exact, so the interval equals the per-thread
 // solver's up to how the compiler contracts the bound's multiply-adds.
-// Agents whose 2D LP is empty continue with the per-thread least-penetration
-// LP.
+// Every agent first runs the per-thread least-penetration LP and makes the
+// per-thread scheme's feasibility decision (solve_velocity); agents left
+// undecided share the lockstep 2D LP, and those whose 2D LP is empty take
+// the least-penetration result.
 // ---------------------------------------------------------------------------
 
 // order-preserving map of floats to ints (for atomic min/max)
@@ -507,8 +539,9 @@ constexpr int kWorkUnitMaxBlock = 128;
 // lines_base is the block's line array (agent a, line j at [j * B + a]).
 __device__ __forceinline__ int solve_velocity_work_units(const float4* __restrict__ lines_base,
                                                          int n, float vmax, float vpx,
-                                                         float vpy, float& vx, float& vy,
-                                                         float& tstar, int& work) {
+                                                         float vpy, float sx, float sy,
+                                                         float& vx, float& vy, float& tstar,
+                                                         int& work) {
     __shared__ int s_tl[kWorkUnitMaxBlock], s_tr[kWorkUnitMaxBlock];
     __shared__ int s_empty[kWorkUnitMaxBlock], s_list[kWorkUnitMaxBlock];
     __shared__ float s_tol[kWorkUnitMaxBlock];
@@ -535,7 +568,17 @@ __device__ __forceinline__ int solve_velocity_work_units(const float4* __restric
     atomicMax(&s_kmax, n);
     __syncthreads();
     const int kmax = s_kmax;
+    // the least-penetration LP first, with the per-thread scheme's decision
+    // (solve_velocity): a t* above 0.1 tol without rounding fallback is
+    // infeasible, and that agent only takes part in the block's lockstep
+    float v3x = 0.0f, v3y = 0.0f, t3 = 0.0f;
+    uint32_t act = 0u;
     bool live = true;
+    if (n > 0) {
+        bool fallback = false;
+        t3 = lp3_min_penetration(L, B, n, vmax, sx, sy, v3x, v3y, work, act, &fallback);
+        live = !(t3 > 0.1f * tol && !fallback);
+    }
     for (int i = 0; i < kmax; ++i) {
         bool need = false;
         float4 li = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -585,9 +628,6 @@ __device__ __forceinline__ int solve_velocity_work_units(const float4* __restric
         __syncthreads();
     }
     if (live) return 0;
-    float v3x, v3y;
-    uint32_t act = 0u;
-    const float t3 = lp3_min_penetration(L, B, n, vmax, v3x, v3y, work, act);
     tstar = t3;
     vx = v3x;
     vy = v3y;

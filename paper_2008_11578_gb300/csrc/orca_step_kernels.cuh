@@ -922,13 +922,14 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     uint32_t act = 0u;
     const int infeasible =
         WORK_UNITS ? solve_velocity_work_units(smem_lines, active ? nlines : 0, vmax, vpx, vpy,
-                                               vx, vy, tstar, work)
+                                               v.x, v.y, vx, vy, tstar, work)
         : LP == LP_WARP
             ? solve_velocity_warp(smem_lines, (int)(threadIdx.x & ~31u), active ? nlines : 0, vmax,
                                   vpx, vpy, vx, vy, tstar, work)
         : LP == LP_ENUMERATION
             ? solve_velocity_enumeration(L, stride, nlines, vmax, vpx, vpy, vx, vy, tstar, work)
-            : solve_velocity(L, stride, nlines, vmax, vpx, vpy, vx, vy, tstar, work, act);
+            : solve_velocity(L, stride, nlines, vmax, vpx, vpy, v.x, v.y, vx, vy, tstar, work,
+                             act);
     if (MODE == MODE_COUNT) clk[3] = clock64();
     if (!active) return;
     const uint8_t flags = (uint8_t)(infeasible | (any_overlap ? 4 : 0));

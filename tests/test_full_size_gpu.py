@@ -14,6 +14,7 @@ import pytest
 import oracle
 from paper_2008_11578_gb300 import api, scenes
 from tests.parity_util import cells_oracle, compare
+from tests.parity_util import gpu_step as gpu_step_from
 
 pytestmark = pytest.mark.gpu
 
@@ -122,3 +123,44 @@ def test_clusters_1m_long_run_stays_consistent():
     rng = np.random.default_rng(9)
     compare(cur, g, sel=np.sort(rng.choice(s.n, 3000, replace=False)))
     ds.close()
+
+
+def _jammed_state(scene, n_calls, **shape):
+    import torch
+    ds = api.DeviceScene(scene, "cuda", **shape)
+    for _ in range(n_calls):
+        ds.step(1)
+    torch.cuda.synchronize()
+    assert ds.sync_status() == 0
+    cur = scene.copy()
+    cur.pos, cur.vel = ds.pos.cpu().numpy(), ds.vel.cpu().numpy()
+    ds.close()
+    return cur
+
+
+def test_cluster_density_after_24_steps_every_agent():
+    """Jams form after a few steps: many agents are pressed together with
+    nearly equal velocities, and their LPs sit on the edge of feasibility
+    (t* close to 0, several half-planes through nearly one point).  From the
+    state after 24 steps, one step is compared with the oracle for EVERY
+    agent of the 62,500-agent cluster scene."""
+    s = scenes.clusters(n=62500, side=500.0, n_clusters_axis=2)
+    cur = _jammed_state(s, 24, cell_size=3.0, cell_height=1.5, block_size=64)
+    g = gpu_step_from(cur, cell_size=3.0, cell_height=1.5, block_size=64)
+    st = compare(cur, g)
+    assert st["infeasible_oracle"] > 10000
+
+
+def test_clusters_1m_near_feasible_agents_after_24_calls():
+    """The 1M workload after 24 one-step calls (the state the benchmark
+    times): every agent whose step reports a least penetration t* in
+    (0, 0.2) m/s, the near-feasible band, and 2,000 random agents against
+    the oracle."""
+    s = scenes.clusters()
+    cur = _jammed_state(s, 24, cell_size=3.0, cell_height=1.5, block_size=64)
+    g = gpu_step_from(cur, cell_size=3.0, cell_height=1.5, block_size=64)
+    near = np.nonzero((g["tstar"] > 0.0) & (g["tstar"] < 0.2))[0]
+    rng = np.random.default_rng(24)
+    sel = np.unique(np.concatenate([near, rng.choice(s.n, 2000, replace=False)]))
+    assert len(near) > 100
+    compare(cur, g, sel=sel)
