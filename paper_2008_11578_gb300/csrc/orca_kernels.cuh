@@ -13,8 +13,8 @@
 // first step -- later steps get them from the previous solve -- then the
 // exclusive scan of the cell counts, the scatter into cell order and the
 // ordering by x inside every cell) ->
-// solve (one thread per agent: k-nearest ring search, ORCA lines, LP,
-// integrate) writing pos0/vel0 in sorted order, which becomes the state
+// solve (one thread per agent: k-nearest search over the x-sorted grid rows,
+// ORCA lines, LP, integrate) writing pos0/vel0 in sorted order, which becomes the state
 // order of the next step; the last step of a call writes the caller's
 // arrays instead.
 #pragma once
