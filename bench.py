@@ -332,7 +332,42 @@ def cpu_baseline(scene, cfg, gpu=None, budget_s=2.5, reps=5):
            "single_core": {"value": m1 / t_one, "unit": METRIC, "cores": 1,
                            "sample": f"{m1} agents, best of {reps} after a warm-up"}}
     parity = _parity_stats(scene, r, gpu, sel) if gpu is not None else None
+    out["other_workloads"] = _cpu_baseline_other(reps)
     return out, parity
+
+
+def _cpu_baseline_other(reps, budget_s=1.0):
+    """The oracle on the other workloads' initial states (all host cores,
+    one step, best of ``reps`` after a warm-up, a bounded sample where a
+    whole step would take longer than ``budget_s``)."""
+    import numpy as np
+
+    import oracle
+    from paper_2008_11578_gb300 import scenes
+    rng = np.random.default_rng(2)
+    out = {}
+    sl = scenes.batched()
+    for name, sc in (("open_square_1k", scenes.open_square()),
+                     ("shared_space_65k", scenes.shared_space()),
+                     ("batched_512_largest_scene", max(sl, key=lambda x: x.n)),
+                     ("waypoint_square_4k", scenes.waypoint_square())):
+        probe = np.sort(rng.choice(sc.n, min(sc.n, 500), replace=False))
+        t0 = time.perf_counter()
+        oracle.step(sc, sel=probe)
+        per_agent = (time.perf_counter() - t0) / len(probe)
+        m = int(min(sc.n, max(50, budget_s / max(per_agent, 1e-12))))
+        sel = None if m == sc.n else np.sort(rng.choice(sc.n, m, replace=False))
+        oracle.step(sc, sel=sel)
+        best = min(_timed(lambda: oracle.step(sc, sel=sel)) for _ in range(reps))
+        out[name] = {"value": m / best, "unit": METRIC, "agents": sc.n,
+                     "sample": m, "cores": oracle.num_threads()}
+    return out
+
+
+def _timed(fn):
+    t0 = time.perf_counter()
+    fn()
+    return time.perf_counter() - t0
 
 
 def measure_batched(dev, flush, n_steps=50, tune=True):
