@@ -643,19 +643,24 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     // (d^2, original index): slot m = (d^2, sorted slot j, original index).
     // An admitted candidate shifts only the entries behind it.
     const int k = sc.k;
-    float thr_d = CUDART_INF_F;   // key of the k-th entry once the list is full
+    const float R2 = sc.R2;
+    // d^2 of the k-th entry once the list is full; before, the largest float
+    // below R_n^2, so one comparison admits a candidate (d^2 < R_n^2 and
+    // below the k-th key) and stops a row cursor
+    float thr_d = R2 > 0.0f ? __int_as_float(__float_as_int(R2) - 1) : -1.0f;
     // (d^2, original index) as one 64-bit key: d^2 >= 0, so its bits order
     // like the value, and the index breaks ties in the low word
     unsigned long long thr_key = ~0ull;
     int cnt = 0;
     int n_cand = 0, work = 0;
-    const float R2 = sc.R2;
     const uint32_t* __restrict__ cs = cstart + sc.cell_off;
 
     // candidate j at key distance d2: admitted when within R_n and its
-    // (d^2, original index) key is below the k-th; the entries behind it shift
+    // (d^2, original index) key is below the k-th; the entries behind it
+    // shift.  The agent itself is never a candidate: its own row is scanned
+    // from its neighbouring slots.
     auto consider = [&](int j, float d2) {
-        if (d2 < R2 && d2 <= thr_d && j != s) {
+        if (d2 <= thr_d) {
             const int oj = aux_orig(__ldg(aux + j));
             const unsigned long long key =
                 ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)oj;
@@ -686,8 +691,9 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         // orders each cell by x, and cells of a row are consecutive in x).
         // A row is scanned outward from the agent's x with two cursors: the
         // right one stops at the first candidate right of the agent whose
-        // fl(dx^2 + g2) exceeds the current k-th key (or whose dx^2 reaches
-        // R_n^2), the left one likewise on the left, where g2 is the row's
+        // fl(dx^2 + g2) exceeds the threshold (the k-th key, or the float
+        // below R_n^2 while the list fills), the left one likewise on the
+        // left, where g2 is the row's
         // lower bound of dy^2; every candidate farther along has a larger
         // dx^2, and d^2 = fl(dx^2 + dy^2) >= fl(dx^2 + g2) (rounding is
         // monotone), so none of them can enter the list.
@@ -713,8 +719,8 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         const float fx = fminf(fmaxf(__fmul_rn(__fsub_rn(p.x, sc.origin_x), sc.inv_cell_x) -
                                          (float)cx, 0.0f), 1.0f);
         // scan row ry leftward from jl and rightward from jr while
-        // fl(dx^2 + g2) stays within the current k-th key and dx^2 below
-        // R_n^2; g2 is the row's lower bound of dy^2 (0 for the own row)
+        // fl(dx^2 + g2) stays within the threshold; g2 is the row's lower
+        // bound of dy^2 (0 for the own row)
         auto scan = [&](int jr, int jl, int ry, float g2) {
             const int rb = (int)__ldg(cs + ry * nx), re = (int)__ldg(cs + ry * nx + nx);
             bool ron = jr < re, lon = jl >= rb;
@@ -730,7 +736,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                 if (ron) {
                     const float dx = __fsub_rn(qr.x, p.x);
                     const float dxx = __fmul_rn(dx, dx);
-                    if (dx > 0.0f && (__fadd_rn(dxx, g2) > lim || dxx >= R2)) {
+                    if (dx > 0.0f && __fadd_rn(dxx, g2) > lim) {
                         ron = false;
                     } else {
                         const float dy = __fsub_rn(qr.y, p.y);
@@ -742,7 +748,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                 if (lon) {
                     const float dx = __fsub_rn(ql.x, p.x);
                     const float dxx = __fmul_rn(dx, dx);
-                    if (dx < 0.0f && (__fadd_rn(dxx, g2) > lim || dxx >= R2)) {
+                    if (dx < 0.0f && __fadd_rn(dxx, g2) > lim) {
                         lon = false;
                     } else {
                         const float dy = __fsub_rn(ql.y, p.y);
@@ -776,7 +782,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                     continue;
                 }
                 const float g2 = row_gap2(ry);
-                if (g2 >= R2 || (cnt >= k && g2 > thr_d)) {
+                if (g2 > thr_d) {
                     live = false;
                     continue;
                 }

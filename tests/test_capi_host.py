@@ -59,12 +59,17 @@ def test_workspace_bytes_and_parameter_validation():
                       (dict(debug_flags=1), 1), (dict(debug_flags=128), 1),
                       (dict(debug_flags=10), 1), (dict(debug_flags=14), 1),
                       (dict(debug_flags=18), 1), (dict(debug_flags=24), 1),
-                      (dict(debug_flags=34), 1), (dict(debug_flags=64), 1)]:
+                      (dict(debug_flags=34), 1), (dict(debug_flags=64), 1),
+                      (dict(cell_height=-1.0), 1), (dict(cell_height=float("nan")), 1),
+                      (dict(cell_height=float("inf")), 1)]:
         p = _params(**bad)
         assert L.orca_workspace_bytes(ctypes.byref(p), 10, ctypes.byref(out)) == code, bad
     for good in (2, 4, 6, 8, 12, 16, 20, 32, 36):   # one scheme/checked flag, and/or the test hook
         p = _params(debug_flags=good)
         assert L.orca_workspace_bytes(ctypes.byref(p), 10, ctypes.byref(out)) == 0, good
+    for h in (0.0, 0.25, 8.0):   # 0 = square cells
+        p = _params(cell_height=h)
+        assert L.orca_workspace_bytes(ctypes.byref(p), 10, ctypes.byref(out)) == 0, h
     p = _params()
     assert L.orca_workspace_bytes(ctypes.byref(p), -1, ctypes.byref(out)) == 1
     assert L.orca_workspace_bytes(None, 10, ctypes.byref(out)) == 1
@@ -170,3 +175,18 @@ def test_removal_rejects_null_arguments():
     L = _lib.load()
     n = ctypes.c_int()
     assert L.orca_scene_remove_arrived(None, ctypes.byref(n), None, None) == 1
+
+
+def test_rectangular_cell_parameters():
+    """Cell width and height reach orca_params and size the grid: a width
+    alone means square cells, a height of 0 in the scene's parameters too."""
+    p = scenes.OrcaParams(extent=(50.0, 30.0), cell_size=2.0)
+    cp = api.make_params(p, 4.0, cell_height=0.5)
+    assert (cp.cell_size, cp.cell_height, cp.grid_nx, cp.grid_ny) == (4.0, 0.5, 13, 60)
+    cp = api.make_params(p, 3.0)
+    assert (cp.cell_size, cp.cell_height, cp.grid_nx, cp.grid_ny) == (3.0, 3.0, 17, 10)
+    cp = api.make_params(p)
+    assert (cp.cell_size, cp.cell_height, cp.grid_nx, cp.grid_ny) == (2.0, 2.0, 25, 15)
+    p.cell_height = 1.5
+    cp = api.make_params(p)
+    assert (cp.cell_size, cp.cell_height, cp.grid_nx, cp.grid_ny) == (2.0, 1.5, 25, 20)
