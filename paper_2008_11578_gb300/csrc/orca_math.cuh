@@ -415,16 +415,21 @@ __device__ __forceinline__ bool valley_tie_break(const float4* __restrict__ L, i
                                                  float vpy, float v3x, float v3y, float& ox,
                                                  float& oy, int& work, uint32_t& act) {
     const float atol = 1e-5f * (1.0f + fabsf(t3));
+    // the lines attaining t* (within atol), then the first exactly opposite
+    // pair among them, in the order (i, j) of the line indices
+    unsigned long long amask = 0ull;
+    for (int i = 0; i < n; ++i)
+        if (!(penetration(L[i * stride], v3x, v3y) < t3 - atol)) amask |= 1ull << i;
     int vi = -1, vj = -1;
-    for (int i = 0; i < n && vi < 0; ++i) {
+    for (unsigned long long m = amask; m != 0ull && vi < 0; m &= m - 1ull) {
+        const int i = __ffsll((long long)m) - 1;
         const float4 li = L[i * stride];
-        if (penetration(li, v3x, v3y) < t3 - atol) continue;
-        for (int j = i + 1; j < n; ++j) {
+        for (unsigned long long m2 = m & (m - 1ull); m2 != 0ull; m2 &= m2 - 1ull) {
+            const int j = __ffsll((long long)m2) - 1;
             ++work;
             const float4 lj = L[j * stride];
             if (fabsf(li.z * lj.w - li.w * lj.z) > 2e-7f || li.z * lj.z + li.w * lj.w >= 0.0f)
                 continue;
-            if (penetration(lj, v3x, v3y) < t3 - atol) continue;
             vi = i;
             vj = j;
             break;
