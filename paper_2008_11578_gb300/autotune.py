@@ -23,7 +23,7 @@ import dataclasses
 from . import api
 from ._lib import OrcaError
 
-DEFAULT_ALPHAS = (0.375, 0.5, 0.75, 1.0, 1.5)
+DEFAULT_ALPHAS = (0.375, 0.5, 0.75, 1.0, 1.5, 2.0)
 DEFAULT_ASPECTS = (1.0, 2.0, 4.0, 8.0)
 DEFAULT_BLOCKS = (64, 128)
 

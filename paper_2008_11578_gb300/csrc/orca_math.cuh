@@ -38,7 +38,9 @@ __device__ __forceinline__ float key_d2(float xa, float ya, float xb, float yb) 
 // Which leg of the velocity obstacle is closer: det(q, w_rel) > 0 means the
 // left leg (ties go right).  The decision is defined by the FP64 evaluation
 // q = p_B - p_A, w = v_A - v_B, det = q_x w_y - q_y w_x (no contraction).  An
-// FP32 filter with a rigorous error bound settles almost every pair; only
+// FP32 filter with a rigorous error bound settles almost every pair; an
+// exactly zero w or q (two agents with equal velocities, e.g. both at rest,
+// or at one point) gives det = 0, the right leg; only the remaining
 // near-zero determinants pay for the FP64 evaluation.
 __device__ __forceinline__ bool leg_left(float pax, float pay, float pbx, float pby,
                                          float vax, float vay, float vbx, float vby) {
@@ -49,6 +51,9 @@ __device__ __forceinline__ bool leg_left(float pax, float pay, float pbx, float 
     // |det32 - det_exact| <= ~4u (|a| + |b|); 10u leaves margin
     float bound = 5.97e-7f * (fabsf(a) + fabsf(b));
     if (fabsf(det) > bound) return det > 0.0f;
+    // the FP32 difference of two floats is zero only when they are equal,
+    // so these are exact zeros of q or w (and of the FP64 determinant)
+    if ((wx == 0.0f && wy == 0.0f) || (qx == 0.0f && qy == 0.0f)) return false;
     double qx64 = __dsub_rn((double)pbx, (double)pax);
     double qy64 = __dsub_rn((double)pby, (double)pay);
     double wx64 = __dsub_rn((double)vax, (double)vbx);
@@ -60,14 +65,37 @@ __device__ __forceinline__ bool leg_left(float pax, float pay, float pbx, float 
 // Squared leg length |q|^2 - rho^2 of the velocity obstacle.  For a pair
 // close to touching, the FP32 difference of two nearly equal squares keeps
 // only a few correct bits (|q|^2 = 1.000038 against rho^2 = 1 loses three
-// digits), and the leg direction inherits that error; there it is redone in
-// FP64, where the products of the FP32 inputs are exact.
+// digits), and the leg direction inherits that error.  There it is redone
+// from error-free FP32 transformations: each square split exactly into a
+// rounded product and its FMA residual, the radius sum into its rounded
+// value and remainder (two-sum), and |q|^2's leading part taken exactly as
+// a two-sum.  The two leading parts, |q|^2 and rho^2, lie within a factor 2
+// of each other here, so their difference is exact (Sterbenz), and only the
+// residuals, each below one ulp of rho^2, are added with rounding.  The
+// result is the exact value up to one final rounding and a few units of
+// 2^-47 rho^2 (as accurate as an FP64 evaluation, without the FP64 pipe).
 __device__ __forceinline__ float leg_l2(float qx, float qy, float ra, float rb, float qq,
                                         float rho2) {
     float l2 = qq - rho2;
     if (l2 < 0.015625f * qq) {
-        const double rho = (double)ra + (double)rb;
-        l2 = (float)((double)qx * qx + (double)qy * qy - rho * rho);
+        // qx^2 = px + ex, qy^2 = py + ey, s^2 = ps + es exactly
+        const float px = __fmul_rn(qx, qx), ex = __fmaf_rn(qx, qx, -px);
+        const float py = __fmul_rn(qy, qy), ey = __fmaf_rn(qy, qy, -py);
+        // ra + rb = s + e exactly
+        const float s = __fadd_rn(ra, rb);
+        const float sb = __fsub_rn(s, ra);
+        const float e = __fadd_rn(__fsub_rn(ra, __fsub_rn(s, sb)), __fsub_rn(rb, sb));
+        const float ps = __fmul_rn(s, s), es = __fmaf_rn(s, s, -ps);
+        // px + py = S + se exactly
+        const float S = __fadd_rn(px, py);
+        const float Sb = __fsub_rn(S, px);
+        const float se = __fadd_rn(__fsub_rn(px, __fsub_rn(S, Sb)), __fsub_rn(py, Sb));
+        // |q|^2 - rho^2 = (S - ps) + (se + ex + ey - es - 2 s e - e^2); e^2 is
+        // below 2^-48 rho^2 and left out
+        const float hi = __fsub_rn(S, ps);
+        const float lo = __fsub_rn(__fsub_rn(__fadd_rn(__fadd_rn(se, ex), ey), es),
+                                   __fmul_rn(__fadd_rn(s, s), e));
+        l2 = __fadd_rn(hi, lo);
     }
     return l2;
 }
