@@ -657,11 +657,14 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
 
     // candidate j at key distance d2: admitted when within R_n and its
     // (d^2, original index) key is below the k-th; the entries behind it
-    // shift.  The agent itself is never a candidate: its own row is scanned
-    // from its neighbouring slots.
-    auto consider = [&](int j, float d2) {
+    // shift.  aj is the word of aux[j] that holds its original index (loaded
+    // with the position, so an admission does not wait on a load).  The
+    // agent itself is never a candidate: its own row is scanned from its
+    // neighbouring slots.
+    const uint32_t* __restrict__ aux_idx = reinterpret_cast<const uint32_t*>(aux) + 1;
+    auto consider = [&](int j, float d2, uint32_t aj) {
         if (d2 <= thr_d) {
-            const int oj = aux_orig(__ldg(aux + j));
+            const int oj = aux_orig(make_uint2(0u, aj));
             const unsigned long long key =
                 ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)oj;
             if (key < thr_key) {
@@ -730,8 +733,15 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
             }
             while (ron || lon) {
                 float2 qr = make_float2(0.0f, 0.0f), ql = make_float2(0.0f, 0.0f);
-                if (ron) qr = pos[jr];
-                if (lon) ql = pos[jl];
+                uint32_t ar = 0u, al = 0u;
+                if (ron) {
+                    qr = pos[jr];
+                    ar = __ldg(aux_idx + 2 * jr);
+                }
+                if (lon) {
+                    ql = pos[jl];
+                    al = __ldg(aux_idx + 2 * jl);
+                }
                 const float lim = thr_d;
                 if (ron) {
                     const float dx = __fsub_rn(qr.x, p.x);
@@ -741,7 +751,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                     } else {
                         const float dy = __fsub_rn(qr.y, p.y);
                         ++n_cand;
-                        consider(jr, __fadd_rn(dxx, __fmul_rn(dy, dy)));
+                        consider(jr, __fadd_rn(dxx, __fmul_rn(dy, dy)), ar);
                         ron = ++jr < re;
                     }
                 }
@@ -753,7 +763,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                     } else {
                         const float dy = __fsub_rn(ql.y, p.y);
                         ++n_cand;
-                        consider(jl, __fadd_rn(dxx, __fmul_rn(dy, dy)));
+                        consider(jl, __fadd_rn(dxx, __fmul_rn(dy, dy)), al);
                         lon = --jl >= rb;
                     }
                 }
