@@ -931,6 +931,46 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         }
     }
 
+    // ---- constraint order of the LP ----
+    // The two half-planes that the agent's current velocity violates most go
+    // first: the least-penetration optimum usually rests on them, so fewer
+    // of the later lines force a re-solve.  The LP's result does not depend
+    // on the order beyond rounding; the recorded active set is mapped back
+    // to the neighbour order below.  Swaps made: slot 0 <-> sw0, then slot
+    // 1 <-> sw1.
+    int sw0 = 0, sw1 = 1;
+    if (nlines > 1) {
+        float pm0 = -CUDART_INF_F, pm1 = -CUDART_INF_F;
+        int im0 = -1, im1 = -1;
+        for (int i = 0; i < nlines; ++i) {
+            const float pv = penetration(L[i * stride], v.x, v.y);
+            if (pv > pm0) {
+                pm1 = pm0;
+                im1 = im0;
+                pm0 = pv;
+                im0 = i;
+            } else if (pv > pm1) {
+                pm1 = pv;
+                im1 = i;
+            }
+        }
+        if (im0 > 0) {
+            const float4 a = L[0];
+            L[0] = L[im0 * stride];
+            L[im0 * stride] = a;
+            sw0 = im0;
+        }
+        if (im1 >= 0 && nlines > 2) {
+            const int b = im1 == 0 ? sw0 : im1;   // where the second line is now (>= 1)
+            if (b > 1) {
+                const float4 a = L[stride];
+                L[stride] = L[b * stride];
+                L[b * stride] = a;
+                sw1 = b;
+            }
+        }
+    }
+
     if (MODE == MODE_COUNT) clk[2] = clock64();
 
     // ---- velocity LP, least-penetration fallback ----
@@ -994,7 +1034,11 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     if (MODE == MODE_RECORD && dbg.act != nullptr) {
         const int nl = act_nlines(act);
         for (int m = 0; m < nl; ++m) {
-            const int li = act_line(act, m);
+            // the LP's line index in the neighbour order (undo the swaps)
+            int li = act_line(act, m);
+            li = li == 1 ? sw1 : (li == sw1 ? 1 : li);
+            li = li == 0 ? sw0 : (li == sw0 ? 0 : li);
+            act = (act & ~(31u << (8 + 8 * m))) | ((uint32_t)li << (8 + 8 * m));
             act |= ((capbits >> li) & 1u) << (13 + 8 * m);
             act |= ((ovbits >> li) & 1u) << (14 + 8 * m);
         }
