@@ -819,23 +819,20 @@ def run_ours(args):
     # ---- end to end through the public API from pinned host buffers ----
     e2e = None
     if not args.no_e2e:
-        hp = torch.empty((n, 2), dtype=torch.float32, pin_memory=True)
-        hv = torch.empty((n, 2), dtype=torch.float32, pin_memory=True)
-        op = torch.empty((n, 2), dtype=torch.float32, pin_memory=True)
-        ov = torch.empty((n, 2), dtype=torch.float32, pin_memory=True)
-        hp.copy_(ds.pos)
-        hv.copy_(ds.vel)
+        # the caller's state as one pinned host block (positions then
+        # velocities), the layout of the scene's device state: one copy each way
+        hs = torch.empty((2, n, 2), dtype=torch.float32, pin_memory=True)
+        os_ = torch.empty((2, n, 2), dtype=torch.float32, pin_memory=True)
+        hs.copy_(ds.state)
         eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
         barrier()
         for k in range(args.steps):
             flush.zero_()
             eev[k][0].record(stream)
-            ds.pos.copy_(hp, non_blocking=True)
-            ds.vel.copy_(hv, non_blocking=True)
+            ds.state.copy_(hs, non_blocking=True)
             ds.step(1)
-            op.copy_(ds.pos, non_blocking=True)
-            ov.copy_(ds.vel, non_blocking=True)
+            os_.copy_(ds.state, non_blocking=True)
             eev[k][1].record(stream)
         barrier()
         e_total = sum(a.elapsed_time(b) for a, b in eev) / 1e3

@@ -309,7 +309,9 @@ class DeviceScene:
     ``scene`` is a :class:`scenes.Scene` (numpy, caller order).  The device
     tensors ``pos``, ``vel`` and ``wp_idx`` are updated in place by
     :meth:`step`; ``goal``, ``radius``, ``max_speed``, ``type``, ``route``
-    and ``waypoints`` are read-only inputs.
+    and ``waypoints`` are read-only inputs.  ``pos`` and ``vel`` are the two
+    halves of one tensor, ``state`` (shape (2, n, 2)), so the evolving state
+    moves between host and device in a single copy each way.
     """
 
     def __init__(self, scene, device="cuda", cell_size=None, block_size=0, debug=False,
@@ -324,8 +326,12 @@ class DeviceScene:
         def t(a, dt=None):
             return torch.as_tensor(np.ascontiguousarray(a), device=dev, dtype=dt)
 
-        self.pos = t(scene.pos, torch.float32)
-        self.vel = t(scene.vel, torch.float32)
+        # positions and velocities share one allocation ([0] = pos, [1] = vel),
+        # so the evolving state moves between host and device in one copy
+        self.state = torch.empty((2, self.n, 2), dtype=torch.float32, device=dev)
+        self.pos, self.vel = self.state[0], self.state[1]
+        self.pos.copy_(t(scene.pos, torch.float32).reshape(self.n, 2))
+        self.vel.copy_(t(scene.vel, torch.float32).reshape(self.n, 2))
         self.goal = t(scene.goal, torch.float32)
         self.radius = t(scene.radius, torch.float32)
         self.max_speed = t(scene.max_speed, torch.float32)
