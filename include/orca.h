@@ -465,12 +465,13 @@ void orca_batch_destroy(orca_batch *batch);
  *   - Size limit: the call is refused with ORCA_ERR_CAPACITY when
  *     orca_workspace_bytes(params, agents->n_agents) exceeds
  *     ORCA_NOALLOC_SCRATCH_BYTES (about 20,000 agents on a 256 x 256 grid).
- *   - The first call on a device looks up the scratch area's device address
- *     (once per device, with that device current).  Make that first call
- *     before any stream capture.  The address is kept for the life of the
- *     process: after cudaDeviceReset (or anything else that destroys the
- *     device's primary context) it is stale, so do not call this entry
- *     point on that device again.
+ *   - Each call made outside a stream capture looks up the scratch area's
+ *     device address on the current device (cudaGetSymbolAddress), so the
+ *     next such call after a reset of the device's primary context
+ *     (cudaDeviceReset) finds the area at its new address.  Make the first
+ *     call on a device before any stream capture: while the stream is
+ *     capturing the lookup is not made and the last address found on that
+ *     device is used (ORCA_ERR_CUDA if there is none).
  *   - Every call, from every thread and stream, shares the one scratch area
  *     and it keeps the last call's contents; the call clears what has to
  *     start at zero.  Calls that overlap on the GPU race with each other:

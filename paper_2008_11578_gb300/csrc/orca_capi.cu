@@ -1162,11 +1162,17 @@ constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 char* g_noalloc_base[kNoallocMaxDevices] = {};
 
-// Device address of the scratch area on the current device, looked up once
-// per device.  Returns nullptr on failure.
-char* noalloc_base(int dev) {
+// Device address of the scratch area on the current device.  Outside a
+// stream capture it is looked up on every call (after a reset of the
+// device's primary context the module is loaded again, at a new address);
+// while the stream is capturing the lookup, which may load the module, is
+// not made and the last address found is returned (nullptr if none, or on
+// failure).
+char* noalloc_base(int dev, cudaStream_t stream) {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (g_noalloc_base[dev] == nullptr) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) return nullptr;
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr)
             return nullptr;
@@ -1194,9 +1200,9 @@ extern "C" int orca_step_noalloc(const orca_params* params, const orca_agents* a
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return ORCA_ERR_CUDA;
     if (dev < 0 || dev >= kNoallocMaxDevices) return ORCA_ERR_CAPACITY;
-    char* w = noalloc_base(dev);
-    if (w == nullptr) return ORCA_ERR_CUDA;
     cudaStream_t stm = (cudaStream_t)stream;
+    char* w = noalloc_base(dev, stm);
+    if (w == nullptr) return ORCA_ERR_CUDA;
 
     // a pipeline over the scratch area, held on the host stack
     Pipeline P;
