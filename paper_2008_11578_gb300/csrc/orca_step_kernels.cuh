@@ -932,12 +932,14 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     }
 
     // ---- constraint order of the LP ----
-    // The two half-planes that the agent's current velocity violates most go
-    // first: the least-penetration optimum usually rests on them, so fewer
-    // of the later lines force a re-solve.  The LP's result does not depend
-    // on the order beyond rounding; the recorded active set is mapped back
-    // to the neighbour order below.  Swaps made: slot 0 <-> sw0, then slot
-    // 1 <-> sw1.
+    // Half-planes in decreasing penetration at the agent's current velocity:
+    // the least-penetration optimum usually rests on the most violated ones,
+    // so fewer of the later lines force a re-solve.  The two most violated
+    // go first (swaps: slot 0 <-> sw0, then slot 1 <-> sw1); with at most 16
+    // lines the rest follow in sorted order (insertion sort, ties keep their
+    // order).  The LP's result does not depend on the order beyond rounding;
+    // the recorded active set is mapped back to the neighbour order below,
+    // through perm (slot -> neighbour index, 4 bits per slot) when sorted.
     int sw0 = 0, sw1 = 1;
     if (nlines > 1) {
         float pm0 = -CUDART_INF_F, pm1 = -CUDART_INF_F;
@@ -968,6 +970,35 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                 L[b * stride] = a;
                 sw1 = b;
             }
+        }
+    }
+    auto nib = [](uint64_t q, int i) { return (uint32_t)((q >> (4 * i)) & 15ull); };
+    auto put = [](uint64_t q, int i, uint32_t x) {
+        return (q & ~(15ull << (4 * i))) | ((uint64_t)x << (4 * i));
+    };
+    uint64_t perm = 0ull;
+    if (MODE == MODE_RECORD && nlines <= 16) {
+        perm = 0xFEDCBA9876543210ull;
+        const uint32_t a0 = nib(perm, sw0);
+        perm = put(put(perm, sw0, nib(perm, 0)), 0, a0);
+        const uint32_t a1 = nib(perm, sw1);
+        perm = put(put(perm, sw1, nib(perm, 1)), 1, a1);
+    }
+    if (nlines <= 16) {
+        for (int m = 3; m < nlines; ++m) {
+            const float4 e = L[m * stride];
+            const float pe = penetration(e, v.x, v.y);
+            const uint32_t em = MODE == MODE_RECORD ? nib(perm, m) : 0u;
+            int at = m;
+            while (at > 2) {
+                const float4 f = L[(at - 1) * stride];
+                if (!(penetration(f, v.x, v.y) < pe)) break;
+                L[at * stride] = f;
+                if (MODE == MODE_RECORD) perm = put(perm, at, nib(perm, at - 1));
+                --at;
+            }
+            L[at * stride] = e;
+            if (MODE == MODE_RECORD) perm = put(perm, at, em);
         }
     }
 
@@ -1034,10 +1065,14 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     if (MODE == MODE_RECORD && dbg.act != nullptr) {
         const int nl = act_nlines(act);
         for (int m = 0; m < nl; ++m) {
-            // the LP's line index in the neighbour order (undo the swaps)
+            // the LP's line index in the neighbour order
             int li = act_line(act, m);
-            li = li == 1 ? sw1 : (li == sw1 ? 1 : li);
-            li = li == 0 ? sw0 : (li == sw0 ? 0 : li);
+            if (nlines <= 16) {
+                li = (int)nib(perm, li);
+            } else {   // undo the two swaps
+                li = li == 1 ? sw1 : (li == sw1 ? 1 : li);
+                li = li == 0 ? sw0 : (li == sw0 ? 0 : li);
+            }
             act = (act & ~(31u << (8 + 8 * m))) | ((uint32_t)li << (8 + 8 * m));
             act |= ((capbits >> li) & 1u) << (13 + 8 * m);
             act |= ((ovbits >> li) & 1u) << (14 + 8 * m);
