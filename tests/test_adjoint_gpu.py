@@ -96,9 +96,15 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-@pytest.mark.parametrize("side,n_steps,ckpt", [(40.0, 12, 5), (60.0, 10, 4)])
-def test_adjoint_matches_fp64_reference_on_gpu_trajectory(side, n_steps, ckpt):
+# k = 16 and 17 straddle the step's constraint order: with up to 16 lines the
+# LP takes them sorted by penetration and the recorded active set is mapped
+# back through the packed slot permutation, with more only the two most
+# violated are moved to the front
+@pytest.mark.parametrize("side,n_steps,ckpt,k", [(40.0, 12, 5, 10), (60.0, 10, 4, 10),
+                                                 (60.0, 10, 4, 16), (60.0, 10, 4, 17)])
+def test_adjoint_matches_fp64_reference_on_gpu_trajectory(side, n_steps, ckpt, k):
     s = scenes.waypoint_square(n_ped=400, n_veh=16, side=side, seed=43)
+    s.params.max_neighbors = k
     rng = np.random.default_rng(5)
     delta = rng.normal(0, 0.2, (n_steps, s.n, 2)).astype(np.float32)
     g = _cuda_grads(s, n_steps, ckpt, delta, want_state0=True)

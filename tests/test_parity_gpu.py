@@ -173,11 +173,25 @@ def test_single_agent_moves_to_goal():
 
 
 def test_k_zero_and_k_32():
-    for k in (0, 1, 32):
+    # 16 and 17 straddle the LP's constraint order (all lines sorted by
+    # penetration up to 16 lines, only the two most violated first above)
+    for k in (0, 1, 16, 17, 32):
         s = scenes.open_square(700, 30.0, seed=10)
         s.params.max_neighbors = k
         g = gpu_step(s)
         compare(s, g)
+
+
+def test_k_16_with_vehicle_kinematic_lines():
+    """k = 16: pedestrians' 16 half-planes take the sorted constraint order,
+    a vehicle's 16 + 3 kinematic half-planes take the two-most-violated
+    order."""
+    s = scenes.shared_space(n_ped=3000, n_veh=200, side=90.0, seed=15)
+    s.params.max_neighbors = 16
+    s.params.vehicle_turn_rate, s.params.vehicle_accel = 0.8, 2.0
+    g = gpu_step(s)
+    assert g["status"] == 0
+    compare(s, g, sel=np.arange(0, s.n, 2))
 
 
 def test_grid_at_the_cell_limit():
