@@ -780,7 +780,8 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
         bool up = true, down = true;   // rows cy + m / cy - m left to visit
         for (int m = 1; up || down; ++m) {
             // the nearer of the two rows first
-            const int first = row_gap2(cy + m) < row_gap2(cy - m) ? 1 : 0;
+            const float gd = row_gap2(cy - m), gu = row_gap2(cy + m);
+            const int first = gu < gd ? 1 : 0;
 #pragma unroll
             for (int side0 = 0; side0 < 2; ++side0) {
                 const int side = side0 ^ first;
@@ -791,7 +792,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                     live = false;
                     continue;
                 }
-                const float g2 = row_gap2(ry);
+                const float g2 = side == 0 ? gd : gu;
                 if (g2 > thr_d) {
                     live = false;
                     continue;
