@@ -769,36 +769,46 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                 }
             }
         };
-        auto scan_row = [&](int ry, float g2) {
+        // Rows in visiting order, through one call site of the row scan: the
+        // agent's own row (ring 0) from its neighbouring slots, then ring by
+        // ring the nearer of rows cy - m and cy + m first, each from the
+        // agent's x interpolated inside the row's cell of column cx.  A side
+        // ends at the grid edge or at the first row whose y gap is beyond the
+        // threshold.
+        bool up = true, down = true;   // rows cy + m / cy - m left to visit
+        int m = 0, so = 2;             // ring, and the next of its two sides
+        float gd = 0.0f, gu = 0.0f;    // the ring's y gaps below and above
+        int first = 0;
+        int ry = cy, jr = s + 1, jl = s - 1;
+        float g2 = 0.0f;
+        for (;;) {
+            scan(jr, jl, ry, g2);
+            bool found = false;
+            while (!found && (up || down)) {
+                if (so == 2) {
+                    ++m;
+                    so = 0;
+                    gd = row_gap2(cy - m);
+                    gu = row_gap2(cy + m);
+                    first = gu < gd ? 1 : 0;
+                }
+                const int side = so ^ first;
+                ++so;
+                if (!(side == 0 ? down : up)) continue;
+                ry = side == 0 ? cy - m : cy + m;
+                g2 = side == 0 ? gd : gu;
+                if (ry < 0 || ry >= ny || g2 > thr_d) {
+                    if (side == 0) down = false;
+                    else up = false;
+                    continue;
+                }
+                found = true;
+            }
+            if (!found) break;
             const int c = ry * nx + cx;
             const int b = (int)__ldg(cs + c), e = (int)__ldg(cs + c + 1);
-            const int j0 = min(b + (int)(fx * (float)(e - b)), e);
-            scan(j0, j0 - 1, ry, g2);
-        };
-
-        scan(s + 1, s - 1, cy, 0.0f);   // the agent's own row: start beside the agent
-        bool up = true, down = true;   // rows cy + m / cy - m left to visit
-        for (int m = 1; up || down; ++m) {
-            // the nearer of the two rows first
-            const float gd = row_gap2(cy - m), gu = row_gap2(cy + m);
-            const int first = gu < gd ? 1 : 0;
-#pragma unroll
-            for (int side0 = 0; side0 < 2; ++side0) {
-                const int side = side0 ^ first;
-                bool& live = side == 0 ? down : up;
-                if (!live) continue;
-                const int ry = side == 0 ? cy - m : cy + m;
-                if (ry < 0 || ry >= ny) {
-                    live = false;
-                    continue;
-                }
-                const float g2 = side == 0 ? gd : gu;
-                if (g2 > thr_d) {
-                    live = false;
-                    continue;
-                }
-                scan_row(ry, g2);
-            }
+            jr = min(b + (int)(fx * (float)(e - b)), e);
+            jl = jr - 1;
         }
     }
 
