@@ -63,6 +63,7 @@ BIN_BYTES_METHOD = 88
 # new positions) and read the previous step's state instead of the staged one.
 BIN_BYTES_KERNEL_FIRST, BIN_BYTES_KERNEL_LATER, BIN_BYTES_CELL = 65 + 24 + 68, 24 + 68, 12
 FP32_LANES = 128    # FP32 lanes per SM (sm_103a)
+N_COUNTERS = 13     # work tallies of the counting solve variant (layout in orca.h)
 
 
 def _source_hash():
@@ -565,7 +566,7 @@ def measure_vehicle_share(dev, flush, cell, cell_h, block, steps=10, warmup=3):
             ts.append(e0.elapsed_time(e1))
         ds.pos.copy_(saved[0])
         ds.vel.copy_(saved[1])
-        counters = torch.zeros(9, dtype=torch.int64, device=dev)
+        counters = torch.zeros(N_COUNTERS, dtype=torch.int64, device=dev)
         api.orca_scene_set_counters(ds.handle, counters)
         ds.step(1)
         api.orca_scene_set_counters(ds.handle, None)
@@ -740,7 +741,7 @@ def run_ours(args):
     clocks = clk.summary()
 
     # ---- algorithmic FLOPs of the solve kernel (untimed counting step) ----
-    counters = torch.zeros(9, dtype=torch.int64, device=dev)
+    counters = torch.zeros(N_COUNTERS, dtype=torch.int64, device=dev)
     saved = (ds.pos.clone(), ds.vel.clone())
     api.orca_scene_set_counters(ds.handle, counters)
     ds.step(1)
@@ -767,7 +768,9 @@ def run_ours(args):
                 "solve_share_of_step": statistics.mean(solve_ms) / statistics.mean(step_ms),
                 "flops_per_agent_step": flops / n,
                 "counts_per_agent": {"candidates": c[0] / n, "neighbours": c[1] / n,
-                                     "lp_pairs": c[2] / n, "fallback_frac": c[3] / n},
+                                     "lp_pairs": c[2] / n, "fallback_frac": c[3] / n,
+                                     "klist_admissions": c[9] / n, "klist_shifts": c[10] / n,
+                                     "rows_scanned": c[11] / n, "row_loop_iterations": c[12] / n},
                 # share of a solve thread's clock cycles in each phase (counting
                 # variant, stalls included)
                 "phase_split": {"search": c[5] / c[8], "half_planes": c[6] / c[8],

@@ -244,7 +244,7 @@ int orca_scene_set_bin_events(orca_scene *scene, void *begin, void *end);
 
 /*
  * Work tallies for FLOP accounting, or NULL to stop.  counters is device
- * memory, uint64[9], accumulated (never cleared) by every following step:
+ * memory, uint64[13], accumulated (never cleared) by every following step:
  *   [0] candidate key tests of the neighbour search
  *   [1] ORCA half-planes built
  *   [2] LP pair evaluations (a constraint tested against another inside a
@@ -256,6 +256,11 @@ int orca_scene_set_bin_events(orca_scene *scene, void *begin, void *end);
  *       solve thread from the search on.  Shares of [8] give the phase split
  *       of the solve kernel (time a thread spends in each phase, stalls
  *       included).
+ *   [9] candidates admitted to the sorted k-nearest list
+ *   [10] list entries shifted by those admissions
+ *   [11] grid rows scanned
+ *   [12] iterations of the row scans' two-cursor loop (one candidate of
+ *        each live cursor per iteration)
  * A scene with counters set runs a separate, slower kernel variant.
  */
 int orca_scene_set_counters(orca_scene *scene, unsigned long long *counters);

@@ -124,7 +124,7 @@ def orca_scene_set_bin_events(handle, begin=None, end=None):
 
 def orca_scene_set_counters(handle, counters=None):
     """Accumulate work tallies and phase clock cycles into ``counters``
-    (int64[9] on the device; the layout is in orca.h)."""
+    (int64[13] on the device; the layout is in orca.h)."""
     check(_lib.load().orca_scene_set_counters(handle, _ptr(counters)), "orca_scene_set_counters")
 
 

@@ -135,8 +135,10 @@ constexpr int LP_INCREMENTAL = 0, LP_WORK_UNITS = 1, LP_ENUMERATION = 2, LP_WARP
 // [3] agents that took the least-penetration fallback, [4] agents;
 // thread clock cycles (clock64) summed over agents: [5] neighbour search,
 // [6] preferred velocity and half-planes, [7] velocity LP, [8] the whole
-// thread from the search on (the rest is integration and output).
-constexpr int kNumCounters = 9;
+// thread from the search on (the rest is integration and output); neighbour
+// search: [9] k-list admissions, [10] k-list entries shifted by them,
+// [11] grid rows scanned, [12] iterations of the rows' two-cursor loop.
+constexpr int kNumCounters = 13;
 
 // Device error word bits.  ERR_BIT_STATE: the binning kernel found cell
 // counts that do not sum to the agent count (reported as a timeout: the only

@@ -653,6 +653,7 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
     unsigned long long thr_key = ~0ull;
     int cnt = 0;
     int n_cand = 0, work = 0;
+    int n_adm = 0, n_shift = 0, n_rows = 0, n_iter = 0;   // search tallies (MODE_COUNT)
     const uint32_t* __restrict__ cs = cstart + sc.cell_off;
 
     // candidate j at key distance d2: admitted when within R_n and its
@@ -668,8 +669,10 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
             const unsigned long long key =
                 ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)oj;
             if (key < thr_key) {
+                if (MODE == MODE_COUNT) ++n_adm;
                 int at = min(cnt, k - 1);
                 while (at > 0) {
+                    if (MODE == MODE_COUNT) ++n_shift;
                     const float4 e = L[(at - 1) * stride];
                     const unsigned long long ek =
                         ((unsigned long long)__float_as_uint(e.x) << 32) | __float_as_uint(e.z);
@@ -731,7 +734,9 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                 atomicOr(err, ERR_BIT_CHECK);   // bounds check of the row
                 ron = lon = false;
             }
+            if (MODE == MODE_COUNT) ++n_rows;
             while (ron || lon) {
+                if (MODE == MODE_COUNT) ++n_iter;
                 float2 qr = make_float2(0.0f, 0.0f), ql = make_float2(0.0f, 0.0f);
                 uint32_t ar = 0u, al = 0u;
                 if (ron) {
@@ -1100,7 +1105,11 @@ solve_kernel(int n, SRC src, const float2* __restrict__ pos, const float2* __res
                                               (unsigned long long)(clk[1] - clk[0]),
                                               (unsigned long long)(clk[2] - clk[1]),
                                               (unsigned long long)(clk[3] - clk[2]),
-                                              (unsigned long long)(end - clk[0])};
+                                              (unsigned long long)(end - clk[0]),
+                                              (unsigned long long)n_adm,
+                                              (unsigned long long)n_shift,
+                                              (unsigned long long)n_rows,
+                                              (unsigned long long)n_iter};
 #pragma unroll
         for (int q = 0; q < kNumCounters; ++q) atomicAdd(counters + q, c[q]);
     }
