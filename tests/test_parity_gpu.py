@@ -256,6 +256,43 @@ def test_nonfinite_input_reports_status():
     assert g["status"] == 4
 
 
+def test_counting_variant_computes_the_same_step_and_consistent_tallies():
+    """The counting variant (FLOP accounting and search tallies) is a
+    separate instantiation of the solve kernel: it must compute the plain
+    step bit for bit, and its tallies must fit together (every final list
+    entry was admitted, a shift moves at most k - 1 entries per admission,
+    every agent scans at least its own row, a loop iteration tests at most
+    one candidate per cursor, and the phase clocks add up within the
+    thread's total)."""
+    import torch
+    s = scenes.clusters(n=60000, side=500.0, n_clusters_axis=4, sigma=8.0, seed=31)
+    plain = api.DeviceScene(s, "cuda")
+    counted = api.DeviceScene(s, "cuda")
+    c = torch.zeros(13, dtype=torch.int64, device="cuda")
+    api.orca_scene_set_counters(counted.handle, c)
+    plain.step(1)
+    counted.step(1)
+    torch.cuda.synchronize()
+    assert torch.equal(plain.pos, counted.pos) and torch.equal(plain.vel, counted.vel)
+    api.orca_scene_set_counters(counted.handle, None)
+    dbg = api.DeviceScene(s, "cuda", debug=True)
+    dbg.step(1)
+    torch.cuda.synchronize()
+    lists = int(dbg.dbg["cnt"].sum())
+    k = int(s.params.max_neighbors)
+    t = [int(x) for x in c.cpu().numpy()]
+    n = s.n
+    assert t[4] == n                         # agent updates
+    assert t[1] == lists                     # half-planes built = list entries
+    assert t[9] >= lists                     # admissions
+    assert t[10] <= t[9] * (k - 1)           # shifts
+    assert t[11] >= n                        # rows scanned
+    assert 2 * t[12] >= t[0] and t[12] <= t[0] + 2 * t[11]   # two-cursor iterations
+    assert 0 < t[5] and 0 < t[6] and 0 < t[7] and t[5] + t[6] + t[7] <= t[8]
+    for ds in (plain, counted, dbg):
+        ds.close()
+
+
 def test_launch_count():
     s = scenes.open_square(100, 10.0)
     ds = api.DeviceScene(s)
