@@ -77,11 +77,11 @@ def _source_hash():
     return h.hexdigest()[:16]
 
 
-def _profiled(workload):
-    """Figures of the committed ncu capture of the solve kernel (DRAM bytes
-    per launch, issue-slot and SIMT utilisation), or {} when the CUDA
-    sources changed since that capture."""
-    path = os.path.join(ROOT, "profiles", f"solve_kernel_{workload.split('_', 1)[0]}_1m.md")
+def _profiled(workload, kernel="solve_kernel"):
+    """Figures of the committed ncu capture of a kernel (DRAM bytes per
+    launch, and for the solve kernel issue-slot and SIMT utilisation), or {}
+    when the CUDA sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload.split('_', 1)[0]}_1m.md")
     try:
         txt = open(path).read()
     except OSError:
@@ -783,11 +783,17 @@ def run_ours(args):
     hbm = float(peaks.get("hbm_gbs", 6681.5))
     bin_s = statistics.mean(bin_ms) / 1e3
 
+    # DRAM bytes of a first-step binning launch from the committed capture
+    # (same workload and launch shape), while the sources match it
+    bin_traffic = (_profiled(args.workload, "bin_kernel").get("traffic_bytes_per_launch")
+                   if args.workload == "clusters_1m" else None)
+
     def bin_roof(sec, kernel_bytes_agent, first):
         method_bytes = BIN_BYTES_METHOD * n
         kernel_bytes = kernel_bytes_agent * n + BIN_BYTES_CELL * ncells
         return {"bound": "hbm", "achieved": method_bytes / sec / 1e9, "peak": hbm,
-                "unit": "GB/s", "frac": method_bytes / sec / 1e9 / hbm, "traffic": None,
+                "unit": "GB/s", "frac": method_bytes / sec / 1e9 / hbm,
+                "traffic": bin_traffic if first else None,
                 "kernels": "bin_kernel (cooperative: cell keys, scan, cell order, order by x)",
                 "ms": 1e3 * sec, "bytes_per_step": method_bytes,
                 "bytes_basis": f"{BIN_BYTES_METHOD} B per agent (the method's per-unit figure)",
