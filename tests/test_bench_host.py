@@ -42,6 +42,19 @@ def test_profiled_traffic_follows_the_source_hash(tmp_path, monkeypatch):
     assert bench._profiled_traffic("clusters_1m") is None
 
 
+def test_binning_traffic_comes_from_its_own_capture(tmp_path, monkeypatch):
+    _tree(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h = bench._source_hash()
+    (tmp_path / "profiles" / "bin_kernel_clusters_1m.md").write_text(
+        f"# x\n\nkernel_source_hash: {h}\ntraffic_bytes_per_launch: 54539008\n")
+    assert bench._profiled("clusters_1m", "bin_kernel") == {"traffic_bytes_per_launch": 54539008}
+    assert bench._profiled("clusters_1m") == {}   # the solve kernel has no capture here
+    (tmp_path / "profiles" / "bin_kernel_clusters_1m.md").write_text(
+        "# x\n\nkernel_source_hash: 0000000000000000\ntraffic_bytes_per_launch: 1\n")
+    assert bench._profiled("clusters_1m", "bin_kernel") == {}
+
+
 def test_parity_stats_of_the_cpu_baseline_leg():
     """The bench's parity statistics (oracle sample of the timed workload
     against one GPU step) on CPU: a GPU result equal to the oracle's FP32
