@@ -87,14 +87,14 @@ def _profiled(workload, kernel="solve_kernel"):
     except OSError:
         return {}
     keys = ("kernel_source_hash", "traffic_bytes_per_launch", "issue_active_pct",
-            "simt_efficiency_pct")
+            "simt_efficiency_pct", "warp_instructions_per_launch")
     vals = dict(line.split(": ", 1) for line in txt.splitlines()
                 if line.startswith(tuple(k + ": " for k in keys)))
     if vals.get("kernel_source_hash", "").strip() != _source_hash():
         return {}
     out = {}
     for k, conv in (("traffic_bytes_per_launch", int), ("issue_active_pct", float),
-                    ("simt_efficiency_pct", float)):
+                    ("simt_efficiency_pct", float), ("warp_instructions_per_launch", int)):
         try:
             out[k] = conv(vals[k])
         except (KeyError, ValueError):
@@ -764,6 +764,15 @@ def run_ours(args):
                 # issue slots busy, and active lanes per issued instruction
                 "ncu_issue_active_pct": prof.get("issue_active_pct"),
                 "ncu_simt_efficiency_pct": prof.get("simt_efficiency_pct"),
+                # the issue-slot ceiling: warp instructions of one launch (same
+                # capture) over the live launch time, against one instruction
+                # per scheduler per cycle (4 per SM)
+                "issue": None if "warp_instructions_per_launch" not in prof else {
+                    "achieved_warp_inst_per_s":
+                        prof["warp_instructions_per_launch"] / solve_avg_s,
+                    "peak_warp_inst_per_s": 4.0 * sms * float(sm_mhz) * 1e6,
+                    "frac": prof["warp_instructions_per_launch"] / solve_avg_s
+                            / (4.0 * sms * float(sm_mhz) * 1e6)},
                 "kernel": "solve_kernel", "solve_ms": statistics.mean(solve_ms),
                 "solve_share_of_step": statistics.mean(solve_ms) / statistics.mean(step_ms),
                 "flops_per_agent_step": flops / n,
