@@ -40,6 +40,13 @@
  * on one boundary, or a vertex of two boundaries), which is the plain
  * definition of the problem rather than an incremental algorithm.
  *
+ * Every function here is pinned by the test suite to closed forms, brute
+ * force or invariants.  Parity unpinned: how closely an FP32 implementation
+ * must agree with this oracle at ill-conditioned least-penetration vertices
+ * (nearly parallel or nearly tangent planes, where rounding of the line data
+ * already moves the answer) has no anchor outside this oracle; the active-set
+ * condition number computed here (pinned) marks those agents.
+ *
  * Build: cc -O2 -std=c11 -fopenmp -ffp-contract=off -fPIC -shared
  * (no fast-math: the FP32 decisions need IEEE rounding and no contraction).
  */
